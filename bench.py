@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark: MST edges/s to single-linkage dendrogram on GB300.
+
+Default workload: a random recursive tree of n = 10^8 vertices (m = 10^8 - 1
+edges) with uniform fp32 weights k * 2**-24, seed 1; the 10^8-vertex skewed
+path (w_i = fp32(i + U(0, 0.5))) is timed the same way and reported beside
+it.  One step = one full dendrogram (sort, every contraction level,
+expansion, chain sort, link) through the library's C ABI with the inputs
+resident in HBM; ``e2e`` repeats the step with host buffers (pinned H2D of
+u, v, w and D2H of both outputs inside the timed region).
+
+``--impl reference`` times the CPU oracle (plain C Kruskal, one thread) on a
+bounded sample of the same workload instead.
+
+Prints ONE JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MST edges/s to dendrogram on 1 GB300 + HBM roofline %; batched vs per-tree speedup"
+UNIT = "edges/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "rrt_1e8": dict(family="rrt", n=10**8, seed=1,
+                    desc="random recursive tree, uniform fp32 weights k*2^-24"),
+    "path_1e8": dict(family="path_skewed", n=10**8, seed=2,
+                     desc="skewed path, w_i = fp32(i + U(0,0.5))"),
+    "rrt_1e4": dict(family="rrt", n=10**4, seed=0,
+                    desc="random recursive tree, uniform fp32 weights k*2^-24"),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rrt_1e8")
+    ap.add_argument("--n", type=int, default=None, help="override the vertex count")
+    ap.add_argument("--no-extra", action="store_true", help="skip the path family line")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def make_tree(spec, n=None):
+    from paper_2401_06089_gb300 import inputs
+    n = n or spec["n"]
+    if spec["family"] == "rrt":
+        return inputs.rrt(n, spec["seed"])
+    return inputs.path_skewed(n, spec["seed"])
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) kept only inside [t_start, t_stop]."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.lines = []
+        self.t_start = self.t_stop = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def start(self):
+        self.t_start = time.time()
+
+    def stop(self):
+        self.t_stop = time.time()
+        time.sleep(0.25)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.t_start is not None and not (self.t_start - 0.2 <= t <= self.t_stop + 0.2):
+                continue
+            rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6),
+                              ("sw_thermal_slowdown", 7), ("sw_power_cap", 8)):
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ---- algorithmic bytes per kernel (the model stated in the design doc) ---------
+def sort_weight_bytes(m, launches):
+    """Bytes of the (weight, index) sort passes: first 12 B/edge (read w, write
+    key+index), middle 16, last 28 (read key+index, write perm, gather u, v,
+    write (u, v)); a single pass 24."""
+    if launches == 0:
+        return 0
+    if launches == 1:
+        return 24 * m
+    return (12 + 16 * (launches - 2) + 28) * m
+
+
+def model_bytes(name, prof_entry, m, n_passes_w):
+    e = prof_entry["elements"]
+    per = {"hist_weights": 4, "onesweep_chains": 16, "mark": 16, "ptr_init": 28,
+           "compress": 12, "compact": 30, "expand": 25, "link": 16, "check_offsets": 16,
+           "fill": 4}
+    if name == "onesweep_weights":
+        return sort_weight_bytes(m, n_passes_w) * (prof_entry["launches"] // max(n_passes_w, 1))
+    return per.get(name, 0) * e
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None
+    when the kernel's source changed since the counters were taken."""
+    summary = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    if not os.path.exists(summary):
+        return None
+    text = open(summary).read()
+    m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m2 = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    m3 = re.search(r"source_file:\s*(\S+)", text)
+    if not (m1 and m2 and m3):
+        return None
+    src = os.path.join(ROOT, m3.group(1))
+    if not os.path.exists(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m2.group(1):
+        return None
+    return float(m1.group(1))
+
+
+KERNEL_SOURCES = {"onesweep_weights": "sort", "onesweep_chains": "sort", "hist_weights": "sort",
+                  "mark": "levels", "ptr_init": "levels", "compress": "levels",
+                  "compact": "levels", "expand": "expand", "link": "expand"}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    import numpy as np
+    import oracle
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    spec = WORKLOADS[args.workload]
+    n_sample = min(args.n or spec["n"], 1_000_000)
+    t = make_tree(spec, n_sample)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.dendrogram(t.u, t.v, t.w)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.dendrogram(t.u, t.v, t.w)
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    value = t.m / sec
+    sample = f"{spec['family']} n={n_sample} seed={spec['seed']} (same generator), one thread"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(args, spec),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, spec):
+    n = args.n or spec["n"]
+    return {"workload": f"{args.workload}" + (f"_n{n}" if args.n else ""), "n_vertices": n,
+            "n_edges": n - 1, "family": spec["desc"], "seed": spec["seed"],
+            "layout": "vertices relabelled, edges shuffled, orientations flipped at random",
+            "l2": "inputs larger than L2 (12 B/edge in, 8 B/edge out)" if n > 20_000_000
+            else "working set fits in L2",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+def time_device(pd, torch, t, steps, warmup, profile=True):
+    dev = torch.device("cuda")
+    u = torch.from_numpy(t.u).to(dev)
+    v = torch.from_numpy(t.v).to(dev)
+    w = torch.from_numpy(t.w).to(dev)
+    ws = torch.empty(pd.workspace_size(t.m), dtype=torch.uint8, device=dev)
+    ep = torch.empty(t.m, dtype=torch.int32, device=dev)
+    vp = torch.empty(t.m + 1, dtype=torch.int32, device=dev)
+    for _ in range(warmup):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    return dict(u=u, v=v, w=w, ws=ws, ep=ep, vp=vp)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import paper_2401_06089_gb300 as pd
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = WORKLOADS[args.workload]
+    t = make_tree(spec, args.n)
+    m = t.m
+    pd.load_library()
+
+    u = torch.from_numpy(t.u).to(dev)
+    v = torch.from_numpy(t.v).to(dev)
+    w = torch.from_numpy(t.w).to(dev)
+    ws = torch.empty(pd.workspace_size(m), dtype=torch.uint8, device=dev)
+    ep = torch.empty(m, dtype=torch.int32, device=dev)
+    vp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+
+    _, _, stats = pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp), stats=True)
+    for _ in range(max(args.warmup, 3)):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.6)   # let nvidia-smi start sampling
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pd.profile_start(timing=True)
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler.start()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    prof = pd.profile_read()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * m / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel --------------------------------
+    peak, peak_kind = load_peaks()
+    n_passes_w = prof["onesweep_weights"]["launches"] // max(args.steps, 1)
+    kernels = {}
+    for name, e in prof.items():
+        if e["launches"] == 0:
+            continue
+        b = model_bytes(name, e, m, n_passes_w) if name != "onesweep_weights" else \
+            sort_weight_bytes(m, n_passes_w) * args.steps
+        kernels[name] = {"launches": e["launches"], "ms": e["ms"],
+                         "share": e["ms"] / (ms * args.steps) if e["ms"] else None,
+                         "gbs": b / (e["ms"] / 1e3) / 1e9 if e["ms"] else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms"] or 0.0)
+    dom_e = prof[dom]
+    dom_bytes_total = (sort_weight_bytes(m, n_passes_w) * args.steps if dom == "onesweep_weights"
+                       else model_bytes(dom, dom_e, m, n_passes_w))
+    per_launch_bytes = dom_bytes_total / dom_e["launches"]
+    per_launch_ms = dom_e["ms"] / dom_e["launches"]
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = recorded_traffic(dom)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": per_launch_bytes}
+    path_bytes = sum((sort_weight_bytes(m, n_passes_w) * args.steps if k == "onesweep_weights"
+                      else model_bytes(k, prof[k], m, n_passes_w)) for k in kernels)
+    path_roofline = path_bytes / args.steps / (ms / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_of(args, spec),
+        "roofline": roofline,
+        "path_model_gbs": path_roofline,
+        "path_model_frac": path_roofline / peak,
+        "gpu_launches": sum(e["launches"] for e in prof.values()),
+        "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
+        "kernels": kernels,
+        "levels": stats["level_edges"],
+        "clocks": sampler.summary(),
+    }
+
+    # ---- end to end through the public API with host buffers -------------
+    if not args.no_e2e:
+        uh = torch.from_numpy(t.u).pin_memory()
+        vh = torch.from_numpy(t.v).pin_memory()
+        wh = torch.from_numpy(t.w).pin_memory()
+        eph = torch.empty(m, dtype=torch.int32).pin_memory()
+        vph = torch.empty(m + 1, dtype=torch.int32).pin_memory()
+        k_e2e = max(3, min(args.steps, 10))
+        t_list = []
+        for k in range(k_e2e + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            u.copy_(uh, non_blocking=True)
+            v.copy_(vh, non_blocking=True)
+            w.copy_(wh, non_blocking=True)
+            pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+            eph.copy_(ep, non_blocking=True)
+            vph.copy_(vp, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k > 0:
+                t_list.append(a.elapsed_time(b))
+        e2e_ms = sum(t_list) / len(t_list)
+        if dist:
+            tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+        line["e2e"] = {"value": world * m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                       "h2d_bytes_per_step": 12 * m, "d2h_bytes_per_step": 4 * m + 4 * (m + 1)}
+
+    # ---- the path family at the same size --------------------------------
+    if not args.no_extra and args.workload == "rrt_1e8":
+        spec2 = WORKLOADS["path_1e8"]
+        t2 = make_tree(spec2, args.n)
+        u2 = torch.from_numpy(t2.u).to(dev)
+        v2 = torch.from_numpy(t2.v).to(dev)
+        w2 = torch.from_numpy(t2.w).to(dev)
+        for _ in range(args.warmup):
+            pd.dendrogram(u2, v2, w2, workspace=ws, out=(ep, vp))
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k2 = max(3, args.steps // 2)
+        a.record(stream)
+        for _ in range(k2):
+            pd.dendrogram(u2, v2, w2, workspace=ws, out=(ep, vp))
+        b.record(stream)
+        b.synchronize()
+        ms2 = a.elapsed_time(b) / k2
+        _, _, st2 = pd.dendrogram(u2, v2, w2, workspace=ws, out=(ep, vp), stats=True)
+        line["path_skewed_1e8"] = {"value": t2.m / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
+                                   "steps": k2, "levels": st2["level_edges"]}
+        del u2, v2, w2
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+        oracle.build()
+        n_s = min(args.n or spec["n"], 10_000_000)
+        ts = make_tree(spec, n_s)
+        t0 = time.perf_counter()
+        oracle.dendrogram(ts.u, ts.v, ts.w)
+        sec = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ts.m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{spec['family']} n={n_s} seed={spec['seed']}, "
+                                          f"one thread, {sec:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * pandora.h - C ABI of the GB300 (sm_103a) single-linkage dendrogram library.
+ *
+ * Given a tree of n vertices and m = n - 1 weighted edges (for instance the
+ * minimum spanning tree of a point set), the library computes its
+ * single-linkage dendrogram with the recursive tree-contraction method of
+ * PANDORA (Sao, Prokopenko, Lebrun-Grandie, arXiv 2401.06089):
+ *
+ *   - the edges are sorted by (weight, edge index)          (Section 3.1)
+ *   - every vertex marks its lightest incident edge         (Eq. 1)
+ *   - edges marked by neither endpoint are alpha-edges      (Eq. 2)
+ *   - all other edges are contracted, the tree of alpha-edges is solved
+ *     recursively                                           (Section 3.2)
+ *   - every contracted edge is assigned to a dendrogram chain, the chains
+ *     are sorted and stitched                               (Section 3.3,
+ *                                                            Algorithm 1)
+ *
+ * Output (the parent function P of Section 3.1): for every edge e,
+ * edge_parent[e] is the index of its parent edge, or -1 for the root (the
+ * heaviest edge); for every vertex x, vertex_parent[x] is the index of its
+ * parent edge, which is its lightest incident edge (Eq. 1), or -1 when the
+ * tree has a single vertex.  Results are exact integers: the weights are only
+ * compared, never combined.
+ *
+ * Edge order (Section 3.1 asks for a consistent tie rule; this library reads
+ * it as): edge e is lighter than edge f iff w_e < w_f, or the weights are
+ * equal and e is -0.0 while f is +0.0, or they are equal with the same sign
+ * and e < f (caller index).  -inf, +inf, subnormal and negative weights are
+ * allowed; NaN is an error.
+ *
+ * Memory: every pointer argument is DEVICE memory of the current CUDA device
+ * unless stated otherwise, owned by the caller, and must stay valid until the
+ * work enqueued on `stream` has finished.  The library never frees caller
+ * memory.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).
+ *
+ * Errors: every entry point returns a pandora_status.  Argument errors are
+ * found on the host before any work is enqueued.  Errors found by the kernels
+ * (NaN weight, vertex id out of range, self-loop, input that is not a tree,
+ * an internal iteration limit) are collected in a device status word; the
+ * blocking entry points below read it before returning.  On any error the
+ * contents of the output arrays are unspecified.
+ */
+#ifndef PANDORA_H
+#define PANDORA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pandora_status {
+    PANDORA_OK = 0,
+    PANDORA_ERR_INVALID_ARGUMENT = 1,   /* null pointer, negative size, bad offsets ... */
+    PANDORA_ERR_NAN_WEIGHT = 2,         /* a weight is NaN */
+    PANDORA_ERR_VERTEX_OUT_OF_RANGE = 3,/* an endpoint id is outside [0, n) */
+    PANDORA_ERR_SELF_LOOP = 4,          /* an edge has u == v */
+    PANDORA_ERR_NOT_A_TREE = 5,         /* the edges contain a cycle (so the graph is
+                                           disconnected, since m = n - 1) */
+    PANDORA_ERR_ITERATION_LIMIT = 6,    /* a bounded device loop gave up (never expected
+                                           on valid input) */
+    PANDORA_ERR_OUT_OF_MEMORY = 7,      /* scratch allocation failed */
+    PANDORA_ERR_CUDA = 8,               /* a CUDA runtime call failed */
+    PANDORA_ERR_WORKSPACE_TOO_SMALL = 9 /* caller workspace below pandora_workspace_size() */
+} pandora_status;
+
+/* Per-call statistics (optional output of the *_ws entry points). */
+#define PANDORA_MAX_LEVELS 64
+typedef struct pandora_stats {
+    int32_t n_levels;                         /* contraction levels run (Section 3.2) */
+    int32_t reserved;
+    int64_t level_edges[PANDORA_MAX_LEVELS];  /* edges of level l (level 0 = all edges) */
+    int64_t level_vertices[PANDORA_MAX_LEVELS];
+} pandora_stats;
+
+/*
+ * Dendrogram of one tree (Algorithm 1).
+ *   u, v          int32[n_edges]: endpoints, vertex ids in [0, n_edges].
+ *   w             float[n_edges]: weights.
+ *   n_edges       m >= 0; the tree has n = m + 1 vertices; m + 1 <= INT32_MAX.
+ *   edge_parent   int32[n_edges] out (may be NULL when n_edges == 0).
+ *   vertex_parent int32[n_edges + 1] out.
+ * Scratch memory is taken stream-ordered from a library-owned CUDA memory
+ * pool.  The call blocks the calling host thread until the result is complete
+ * on `stream` (it reads the level sizes back between contraction levels) and
+ * returns the device-detected status.
+ */
+int pandora_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                       int32_t *edge_parent, int32_t *vertex_parent, void *stream);
+
+/*
+ * Bytes of caller workspace that pandora_dendrogram_ws / _batched_ws need for
+ * a total of `total_edges` edges in `n_trees` trees (n_trees = 1 for a single
+ * tree).  Writes the size to *bytes.  Host only; enqueues nothing.
+ */
+int pandora_workspace_size(int64_t total_edges, int64_t n_trees, size_t *bytes);
+
+/*
+ * As pandora_dendrogram, with caller-provided device workspace (at least
+ * pandora_workspace_size(n_edges, 1) bytes, 256-byte aligned) and optional
+ * host-memory statistics (NULL to skip).  Allocates nothing.
+ */
+int pandora_dendrogram_ws(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                          int32_t *edge_parent, int32_t *vertex_parent, void *workspace,
+                          size_t workspace_bytes, pandora_stats *stats, void *stream);
+
+/*
+ * Dendrograms of many independent trees in one pass (the whole batch is
+ * processed as one forest: one sort, one contraction loop, one expansion).
+ *   edge_offsets  int64[n_trees + 1], DEVICE memory: tree t owns the edges
+ *                 [edge_offsets[t], edge_offsets[t+1]) and the vertices
+ *                 [edge_offsets[t] + t, edge_offsets[t+1] + t + 1) of the
+ *                 packed arrays.  edge_offsets[0] = 0, non-decreasing.
+ *   total_edges   must equal edge_offsets[n_trees] (checked on the device).
+ *   u, v          int32[total_edges]: TREE-LOCAL vertex ids (0 .. n_t - 1).
+ *   w             float[total_edges].
+ *   edge_parent   int32[total_edges] out: tree-local edge ids or -1.
+ *   vertex_parent int32[total_edges + n_trees] out: tree-local edge ids, or -1
+ *                 for a tree with a single vertex.
+ * total_edges + n_trees <= INT32_MAX.  Blocking, like pandora_dendrogram.
+ * Every tree's result equals the result of pandora_dendrogram on that tree.
+ */
+int pandora_dendrogram_batched(const int32_t *u, const int32_t *v, const float *w,
+                               const int64_t *edge_offsets, int64_t n_trees, int64_t total_edges,
+                               int32_t *edge_parent, int32_t *vertex_parent, void *stream);
+
+/* As pandora_dendrogram_batched with caller workspace
+ * (pandora_workspace_size(total_edges, n_trees) bytes) and optional stats. */
+int pandora_dendrogram_batched_ws(const int32_t *u, const int32_t *v, const float *w,
+                                  const int64_t *edge_offsets, int64_t n_trees,
+                                  int64_t total_edges, int32_t *edge_parent,
+                                  int32_t *vertex_parent, void *workspace,
+                                  size_t workspace_bytes, pandora_stats *stats, void *stream);
+
+/*
+ * Optional instrumentation (process-wide, thread-safe, host memory).
+ * pandora_profile_start resets the counters of every kernel of the path.  The
+ * library always counts launches; with with_timing != 0 it also records a
+ * CUDA event pair around every launch on the launching stream and adds the
+ * elapsed time to the kernel's total when the call completes.
+ * pandora_profile_read copies the counters into *out.  Enqueues nothing.
+ */
+#define PANDORA_PROFILE_SLOTS 16
+typedef struct pandora_profile {
+    int32_t n_kernels;
+    int32_t timing;                               /* 1 when total_ms is valid */
+    char name[PANDORA_PROFILE_SLOTS][32];
+    int64_t launches[PANDORA_PROFILE_SLOTS];
+    int64_t elements[PANDORA_PROFILE_SLOTS];      /* items processed (edges or vertices) */
+    double total_ms[PANDORA_PROFILE_SLOTS];
+} pandora_profile;
+
+int pandora_profile_start(int with_timing);
+int pandora_profile_read(pandora_profile *out);
+
+/* Static description of a status code (never NULL). */
+const char *pandora_status_string(int status);
+
+/* Library version as 10000 * major + 100 * minor + patch. */
+int pandora_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PANDORA_H */

@@ -1,0 +1,19 @@
+"""GB300-native single-linkage dendrograms of weighted trees (PANDORA method).
+
+The compute path is a C-ABI CUDA library (``libpandora.so``, sm_103a) whose
+entry points are declared in ``include/pandora.h``; this package is a thin
+ctypes binding over it.  Nothing is loaded at import time; the first call
+loads the library and raises if it is missing or no GPU is present.  There is
+no CPU fallback.
+"""
+from ._binding import (  # noqa: F401
+    PandoraError,
+    dendrogram,
+    dendrogram_batched,
+    library_path,
+    profile_read,
+    profile_start,
+    load_library,
+    status_string,
+    workspace_size,
+)

@@ -1,0 +1,236 @@
+"""ctypes binding of libpandora.so (argument marshalling only).
+
+Every function here checks its tensors, hands raw device pointers and the
+current CUDA stream to the C ABI of ``include/pandora.h`` and raises
+``PandoraError`` on a non-zero status.  No step of the dendrogram is computed
+in Python, and there is no CPU fallback: without the library or a GPU the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_NAME = "libpandora.so"
+_lock = threading.Lock()
+_lib = None
+
+MAX_LEVELS = 64
+
+STATUS_NAMES = {
+    0: "PANDORA_OK",
+    1: "PANDORA_ERR_INVALID_ARGUMENT",
+    2: "PANDORA_ERR_NAN_WEIGHT",
+    3: "PANDORA_ERR_VERTEX_OUT_OF_RANGE",
+    4: "PANDORA_ERR_SELF_LOOP",
+    5: "PANDORA_ERR_NOT_A_TREE",
+    6: "PANDORA_ERR_ITERATION_LIMIT",
+    7: "PANDORA_ERR_OUT_OF_MEMORY",
+    8: "PANDORA_ERR_CUDA",
+    9: "PANDORA_ERR_WORKSPACE_TOO_SMALL",
+}
+
+
+class PandoraError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        self.name = STATUS_NAMES.get(self.code, "UNKNOWN")
+        super().__init__(f"{what}: {self.name} ({self.code})" if what else self.name)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("level_edges", ctypes.c_int64 * MAX_LEVELS),
+                ("level_vertices", ctypes.c_int64 * MAX_LEVELS)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("n_kernels", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("name", (ctypes.c_char * 32) * 16), ("launches", ctypes.c_int64 * 16),
+                ("elements", ctypes.c_int64 * 16), ("total_ms", ctypes.c_double * 16)]
+
+
+def library_path() -> str:
+    return os.path.join(HERE, _LIB_NAME)
+
+
+def load_library():
+    """Load libpandora.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "paper_2401_06089_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        I64 = ctypes.c_int64
+        SZ = ctypes.c_size_t
+        lib.pandora_dendrogram.argtypes = [P, P, P, I64, P, P, P]
+        lib.pandora_dendrogram_ws.argtypes = [P, P, P, I64, P, P, P, SZ, P, P]
+        lib.pandora_dendrogram_batched.argtypes = [P, P, P, P, I64, I64, P, P, P]
+        lib.pandora_dendrogram_batched_ws.argtypes = [P, P, P, P, I64, I64, P, P, P, SZ, P, P]
+        lib.pandora_workspace_size.argtypes = [I64, I64, ctypes.POINTER(SZ)]
+        lib.pandora_status_string.argtypes = [ctypes.c_int]
+        lib.pandora_status_string.restype = ctypes.c_char_p
+        lib.pandora_version.argtypes = []
+        lib.pandora_profile_start.argtypes = [ctypes.c_int]
+        lib.pandora_profile_read.argtypes = [P]
+        for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
+                     "pandora_dendrogram_batched_ws", "pandora_workspace_size",
+                     "pandora_version", "pandora_profile_start", "pandora_profile_read"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    return load_library().pandora_status_string(int(code)).decode()
+
+
+def workspace_size(total_edges: int, n_trees: int = 1) -> int:
+    out = ctypes.c_size_t(0)
+    st = load_library().pandora_workspace_size(int(total_edges), int(n_trees), ctypes.byref(out))
+    if st:
+        raise PandoraError(st, "pandora_workspace_size")
+    return int(out.value)
+
+
+def profile_start(timing: bool = False) -> None:
+    """Reset the per-kernel counters; with ``timing`` also time every launch."""
+    load_library().pandora_profile_start(1 if timing else 0)
+
+
+def profile_read() -> dict:
+    """{kernel: {"launches", "elements", "ms"}} since the last profile_start."""
+    pr = Profile()
+    load_library().pandora_profile_read(ctypes.byref(pr))
+    out = {}
+    for k in range(pr.n_kernels):
+        name = pr.name[k].value.decode()
+        out[name] = {"launches": int(pr.launches[k]), "elements": int(pr.elements[k]),
+                     "ms": float(pr.total_ms[k]) if pr.timing else None}
+    return out
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check(t, dtype, name, device=None, length=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() != 1 or not t.is_contiguous():
+        raise ValueError(f"{name} must be 1-D and contiguous")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if length is not None and t.numel() != length:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {length}")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+def _stats_dict(st: Stats):
+    n = int(st.n_levels)
+    return {"n_levels": n, "level_edges": [int(x) for x in st.level_edges[:n]],
+            "level_vertices": [int(x) for x in st.level_vertices[:n]]}
+
+
+def dendrogram(u, v, w, *, workspace=None, stats: bool = False, out=None):
+    """Single-linkage dendrogram of one tree (``pandora_dendrogram``).
+
+    u, v: int32 CUDA tensors [m] (vertex ids in [0, m]); w: float32 [m].
+    Returns (edge_parent int32[m], vertex_parent int32[m+1]) on the same
+    device, plus a statistics dict when ``stats`` is True.  ``workspace`` (a
+    uint8 CUDA tensor of at least ``workspace_size(m)`` bytes) avoids the
+    library's own stream-ordered allocation.  ``out`` = (edge_parent,
+    vertex_parent) reuses output tensors.
+    """
+    torch = _torch()
+    lib = load_library()
+    _check(w, torch.float32, "w")
+    dev = w.device
+    m = w.numel()
+    _check(u, torch.int32, "u", dev, m)
+    _check(v, torch.int32, "v", dev, m)
+    if out is None:
+        ep = torch.empty(m, dtype=torch.int32, device=dev)
+        vp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    else:
+        ep, vp = out
+        _check(ep, torch.int32, "edge_parent", dev, m)
+        _check(vp, torch.int32, "vertex_parent", dev, m + 1)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st_out = Stats()
+        if workspace is None and not stats:
+            st = lib.pandora_dendrogram(_ptr(u), _ptr(v), _ptr(w), m, _ptr(ep), _ptr(vp), stream)
+        else:
+            if workspace is None:
+                workspace = torch.empty(workspace_size(m, 1), dtype=torch.uint8, device=dev)
+            st = lib.pandora_dendrogram_ws(_ptr(u), _ptr(v), _ptr(w), m, _ptr(ep), _ptr(vp),
+                                           _ptr(workspace), workspace.numel(),
+                                           ctypes.byref(st_out), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram")
+    if stats:
+        return ep, vp, _stats_dict(st_out)
+    return ep, vp
+
+
+def dendrogram_batched(u, v, w, edge_offsets, *, workspace=None, stats: bool = False, out=None):
+    """Dendrograms of many trees packed by ``edge_offsets`` (int64, CUDA).
+
+    Tree t owns edges [off[t], off[t+1]) and vertices [off[t]+t, off[t+1]+t+1)
+    of the packed arrays; ids in u, v and in the outputs are tree-local.
+    Returns (edge_parent int32[M], vertex_parent int32[M + T]).
+    """
+    torch = _torch()
+    lib = load_library()
+    _check(w, torch.float32, "w")
+    dev = w.device
+    m = w.numel()
+    _check(u, torch.int32, "u", dev, m)
+    _check(v, torch.int32, "v", dev, m)
+    _check(edge_offsets, torch.int64, "edge_offsets", dev)
+    n_trees = edge_offsets.numel() - 1
+    if n_trees < 0:
+        raise ValueError("edge_offsets needs n_trees + 1 entries")
+    if out is None:
+        ep = torch.empty(m, dtype=torch.int32, device=dev)
+        vp = torch.empty(m + n_trees, dtype=torch.int32, device=dev)
+    else:
+        ep, vp = out
+        _check(ep, torch.int32, "edge_parent", dev, m)
+        _check(vp, torch.int32, "vertex_parent", dev, m + n_trees)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st_out = Stats()
+        if workspace is None and not stats:
+            st = lib.pandora_dendrogram_batched(_ptr(u), _ptr(v), _ptr(w), _ptr(edge_offsets),
+                                                n_trees, m, _ptr(ep), _ptr(vp), stream)
+        else:
+            if workspace is None:
+                workspace = torch.empty(workspace_size(m, max(n_trees, 1)), dtype=torch.uint8,
+                                        device=dev)
+            st = lib.pandora_dendrogram_batched_ws(_ptr(u), _ptr(v), _ptr(w), _ptr(edge_offsets),
+                                                   n_trees, m, _ptr(ep), _ptr(vp),
+                                                   _ptr(workspace), workspace.numel(),
+                                                   ctypes.byref(st_out), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram_batched")
+    if stats:
+        return ep, vp, _stats_dict(st_out)
+    return ep, vp

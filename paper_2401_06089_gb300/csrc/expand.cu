@@ -1,0 +1,154 @@
+// Multilevel expansion and chain linking (paper, Sections 3.3.2 and 3.3.3).
+//
+// expand: an edge contracted on level l0 lies inside supervertex S of level
+// l0 + 1.  Going up the levels k = l0+1, l0+2, ..., the edge belongs to the
+// leaf chain hanging from p = P_k(S) (the lightest edge at S on level k,
+// i.e. S's parent in the level-k dendrogram) as soon as it is lighter than
+// p; otherwise S is replaced by its own supervertex on level k + 1.  An edge
+// that no level claims is in the root chain.  The chain is named by the key
+// 2 * rank(p) + side, where side tells which endpoint of p on level k the
+// supervertex S is (a leaf edge heads two chains, one per side; the paper's
+// "2L"/"13R").  Root chains get keys above every such key (one per tree).
+//
+// link: after a stable sort of the keys (edges enter in ascending rank, so
+// every chain leaves sorted by rank) an edge's parent is the next edge of its
+// chain; the heaviest edge of a chain hangs from the chain's head edge p, and
+// the heaviest edge of a root chain is the root (-1).
+#include "kernels.cuh"
+
+namespace pandora {
+
+namespace {
+
+__global__ void __launch_bounds__(256) expand_kernel(const ExpandParams p, const LevelTable t)
+{
+    __shared__ u32 s_h[4 * RADIX];
+    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x)
+        s_h[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 m_round = (p.m + 31) & ~(i64)31;
+    for (i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x; r - lane < m_round; r += stride) {
+        const bool valid = r < p.m;
+        u32 key = 0;
+        if (valid) {
+            const int l0 = p.lev[r];
+            i32 sv = p.start[r];
+            key = NONE;
+            for (int l = l0 + 1; l < p.n_levels; ++l) {
+                const u32 c = __ldg(t.ck[l] + sv);
+                if ((u32)r < (c >> 1)) {   // an isolated supervertex (c = NONE) ends here too
+                    key = c;
+                    break;
+                }
+                sv = __ldg(t.vmap[l] + sv);
+            }
+            if (key == NONE) {
+                u32 tree = 0;
+                if (p.edge_off)
+                    tree = (u32)tree_of_edge(p.edge_off, p.n_trees, (i64)__ldg(p.perm + r));
+                key = p.root_base + tree;
+            }
+            p.keys_out[r] = key;
+        }
+        const u32 k0 = __shfl_sync(0xFFFFFFFFu, key, 0);
+        const u32 vm = __ballot_sync(0xFFFFFFFFu, valid);
+        const bool uniform = __all_sync(0xFFFFFFFFu, key == k0) && vm == 0xFFFFFFFFu;
+        if (uniform) {
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    atomicAdd(&s_h[q * RADIX + ((key >> (8 * q)) & 255)], 32u);
+            }
+        } else if (valid) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                atomicAdd(&s_h[q * RADIX + ((key >> (8 * q)) & 255)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) {
+        const u32 c = s_h[i];
+        if (c)
+            atomicAdd(p.hist + i, c);
+    }
+}
+
+template <bool FOREST>
+__global__ void __launch_bounds__(256) link_kernel(const LinkParams p)
+{
+    const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p.m)
+        return;
+    const u32 k = p.skeys[j];
+    const u32 e = p.svals[j];
+    i32 par;
+    if (j + 1 < p.m && p.skeys[j + 1] == k)
+        par = (i32)p.svals[j + 1];
+    else if (k >= p.root_base)
+        par = -1;
+    else
+        par = (i32)__ldg(p.perm + (k >> 1));
+    if (FOREST && par >= 0)
+        par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, (i64)e));
+    p.edge_parent[e] = par;
+}
+
+__global__ void check_offsets_kernel(const i64 *off, i64 n_trees, i64 total, int *status)
+{
+    const i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_trees)
+        return;
+    const i64 o = off[t];
+    bool bad = (t == 0 && o != 0) || (t == n_trees && o != total) || o < 0 || o > total;
+    if (t > 0 && off[t - 1] > o)
+        bad = true;
+    if (bad)
+        set_status(status, PANDORA_ERR_INVALID_ARGUMENT);
+}
+
+__global__ void fill_kernel(i32 *p, i64 n, i32 value)
+{
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        p[i] = value;
+}
+
+}  // namespace
+
+void launch_expand(const ExpandParams &p, const LevelTable &t, cudaStream_t s)
+{
+    if (p.m <= 0)
+        return;
+    i64 blocks = (p.m + 256 * 8 - 1) / (256 * 8);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    expand_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, t);
+}
+
+void launch_link(const LinkParams &p, cudaStream_t s)
+{
+    if (p.m <= 0)
+        return;
+    const unsigned blocks = (unsigned)((p.m + 255) / 256);
+    if (p.edge_off)
+        link_kernel<true><<<blocks, 256, 0, s>>>(p);
+    else
+        link_kernel<false><<<blocks, 256, 0, s>>>(p);
+}
+
+void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, cudaStream_t s)
+{
+    check_offsets_kernel<<<(unsigned)((n_trees + 1 + 255) / 256), 256, 0, s>>>(off, n_trees, total,
+                                                                              status);
+}
+
+void launch_fill(i32 *p, i64 n, i32 value, cudaStream_t s)
+{
+    if (n <= 0)
+        return;
+    fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, value);
+}
+
+}  // namespace pandora

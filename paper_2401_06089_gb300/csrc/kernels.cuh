@@ -1,0 +1,137 @@
+// Launch interfaces of the kernels of the dendrogram path (internal to the
+// library; the public C ABI is include/pandora.h).
+#pragma once
+
+#include "common.cuh"
+
+namespace pandora {
+
+// ---------------------------------------------------------------------------
+// sort.cu - onesweep LSD radix sort (8-bit digits, decoupled look-back)
+// ---------------------------------------------------------------------------
+constexpr int OS_THREADS = 256;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr int RADIX = 256;
+
+enum OnesweepFlags : int {
+    OS_KEY_FROM_W = 1,    // keys are weight_key(w[i]) computed on the fly
+    OS_GEN_VALS = 2,      // values are the input positions (caller edge index)
+    OS_WRITE_KEYS = 4,    // write the sorted keys
+    OS_GATHER = 8,        // write (u, v) of the value's edge beside it (last pass of
+                          // the weight sort), validating the endpoints
+    OS_FOREST = 16,       // endpoints are tree-local (batched mode)
+};
+
+struct OnesweepParams {
+    const float *w_in;
+    const u32 *keys_in;
+    const u32 *vals_in;
+    u32 *keys_out;
+    u32 *vals_out;
+    i64 n;
+    int shift;
+    const u32 *hist;       // [256] digit counts of this pass
+    u64 *lb;               // [tiles * 256] look-back words, zeroed
+    u32 *tile_counter;     // zeroed
+    int *status;
+    // OS_GATHER
+    const i32 *u;
+    const i32 *v;
+    int2 *ab_out;
+    i64 n_vertices;
+    const i64 *edge_off;   // OS_FOREST
+    i64 n_trees;
+};
+
+__host__ __device__ inline i64 onesweep_tiles(i64 n) { return (n + OS_TILE - 1) / OS_TILE; }
+
+void launch_hist_weights(const float *w, i64 n, u32 *hist /*[4][256]*/, int *status,
+                         cudaStream_t s);
+void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// levels.cu - one contraction level (Eq. 1, Eq. 2, Section 3.2)
+// ---------------------------------------------------------------------------
+constexpr int LV_THREADS = 256;
+constexpr int LV_ITEMS = 8;
+constexpr int LV_TILE = LV_THREADS * LV_ITEMS;
+
+__host__ __device__ inline i64 level_tiles(i64 n) { return (n + LV_TILE - 1) / LV_TILE; }
+
+struct LevelParams {
+    int level;
+    i64 m;                 // edges of this level
+    i64 n;                 // vertices of this level
+    const int2 *ab;        // endpoints (level vertex ids), ascending rank
+    const u32 *er;         // global rank of each edge (nullptr on level 0: rank = index)
+    u32 *min_inc;          // [n] local index of the lightest incident edge
+    i32 *ptr;              // [n] pointer forest scratch
+    i32 *vmap;             // [n] vertex -> supervertex of the next level
+    u32 *ck;               // [n] chain key 2*rank(P(x)) + side (levels >= 1), or nullptr
+    // level 0 only: vertex_parent output
+    const u32 *perm;
+    i32 *vertex_parent;
+    const i64 *edge_off;   // forest mode (nullptr for one tree)
+    i64 n_trees;
+    // next level
+    int2 *ab_next;
+    u32 *er_next;
+    i64 cap_next;          // capacity of ab_next / er_next
+    unsigned char *lev;    // [M] contraction level of each edge (by rank)
+    i32 *start;            // [M] supervertex holding the edge on the next level
+    u64 *lb;               // look-back words (zeroed per kernel)
+    u32 *tile_counter;     // two counters (zeroed)
+    u64 *count_roots;
+    u64 *count_alpha;
+    int *status;
+};
+
+void launch_mark(const LevelParams &p, cudaStream_t s);
+void launch_ptr_init(const LevelParams &p, cudaStream_t s);
+void launch_compress(const LevelParams &p, cudaStream_t s);
+void launch_compact(const LevelParams &p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// expand.cu - multilevel expansion (Section 3.3.2) and chain linking (3.3.3)
+// ---------------------------------------------------------------------------
+struct LevelTable {
+    const u32 *ck[MAX_LEVELS];
+    const i32 *vmap[MAX_LEVELS];
+};
+
+struct ExpandParams {
+    i64 m;
+    int n_levels;
+    const unsigned char *lev;
+    const i32 *start;
+    const u32 *perm;
+    u32 *keys_out;
+    u32 root_base;
+    const i64 *edge_off;   // forest mode
+    i64 n_trees;
+    u32 *hist;             // [4][256] digit histograms of the chain keys
+    int *status;
+};
+
+void launch_expand(const ExpandParams &p, const LevelTable &t, cudaStream_t s);
+
+struct LinkParams {
+    i64 m;
+    const u32 *skeys;      // chain keys sorted
+    const u32 *svals;      // caller edge ids in the same order
+    const u32 *perm;
+    u32 root_base;
+    i32 *edge_parent;
+    const i64 *edge_off;
+    i64 n_trees;
+};
+
+void launch_link(const LinkParams &p, cudaStream_t s);
+
+// forest mode: check the offsets (off[0] == 0, non-decreasing, off[T] == M)
+void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, cudaStream_t s);
+// vertex_parent = -1 for every vertex of an edgeless input
+void launch_fill(i32 *p, i64 n, i32 value, cudaStream_t s);
+
+}  // namespace pandora

@@ -1,0 +1,612 @@
+// Host orchestration and C ABI of the dendrogram library (include/pandora.h).
+//
+// Algorithm 1 of the paper, one tree or a forest of trees at once:
+//   1. sort the edges by (weight, index)              sort.cu   (Section 3.1)
+//   2. contraction levels until no alpha-edge is left levels.cu (Section 3.2)
+//   3. chain key of every edge                        expand.cu (Section 3.3.2)
+//   4. sort by chain key, link each chain             sort.cu, expand.cu (3.3.3)
+// Between levels the host reads back two counters (the next level's edges and
+// vertices) to size the next launches; nothing else leaves the device.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace pandora {
+namespace {
+
+
+// ---- optional instrumentation (pandora_profile_*) -------------------------
+enum Slot : int {
+    K_HIST_WEIGHTS, K_SORT_WEIGHTS, K_MARK, K_PTR_INIT, K_COMPRESS, K_COMPACT, K_EXPAND,
+    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_SLOTS
+};
+const char *const kSlotNames[K_SLOTS] = {
+    "hist_weights", "onesweep_weights", "mark", "ptr_init", "compress", "compact", "expand",
+    "onesweep_chains", "link", "check_offsets", "fill"};
+
+struct Profiler {
+    std::mutex mu;
+    bool timing = false;
+    i64 launches[K_SLOTS] = {};
+    i64 elements[K_SLOTS] = {};
+    double ms[K_SLOTS] = {};
+    std::vector<cudaEvent_t> free_events;
+};
+Profiler &profiler()
+{
+    static Profiler p;
+    return p;
+}
+
+// Counts every launch of one call; with timing on, brackets each launch with
+// a CUDA event pair on the launching stream and adds the elapsed times to the
+// process-wide totals once the call's work is complete.
+class CallTimer {
+  public:
+    explicit CallTimer(cudaStream_t s) : s_(s)
+    {
+        Profiler &p = profiler();
+        std::lock_guard<std::mutex> lock(p.mu);
+        timing_ = p.timing;
+    }
+    ~CallTimer() { flush(); }
+
+    template <class F> void launch(int slot, i64 elements, F &&f)
+    {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timing_) {
+            a = get();
+            b = get();
+            if (a)
+                cudaEventRecord(a, s_);
+        }
+        f();
+        if (timing_ && b)
+            cudaEventRecord(b, s_);
+        recs_.push_back({slot, elements, a, b});
+    }
+
+  private:
+    struct Rec {
+        int slot;
+        i64 elements;
+        cudaEvent_t a, b;
+    };
+    cudaEvent_t get()
+    {
+        Profiler &p = profiler();
+        {
+            std::lock_guard<std::mutex> lock(p.mu);
+            if (!p.free_events.empty()) {
+                cudaEvent_t e = p.free_events.back();
+                p.free_events.pop_back();
+                return e;
+            }
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess)
+            return nullptr;
+        return e;
+    }
+    void flush()
+    {
+        if (recs_.empty())
+            return;
+        if (timing_)
+            cudaStreamSynchronize(s_);
+        Profiler &p = profiler();
+        std::lock_guard<std::mutex> lock(p.mu);
+        for (const Rec &r : recs_) {
+            p.launches[r.slot] += 1;
+            p.elements[r.slot] += r.elements;
+            if (r.a && r.b) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+                    p.ms[r.slot] += ms;
+            }
+            if (r.a)
+                p.free_events.push_back(r.a);
+            if (r.b)
+                p.free_events.push_back(r.b);
+        }
+        recs_.clear();
+        cudaGetLastError();
+    }
+    cudaStream_t s_;
+    bool timing_ = false;
+    std::vector<Rec> recs_;
+};
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_inc, ptr, vmap0;
+    size_t kept_ck, kept_vmap, abX, erX, abY, erY, lev, start, total;
+    i64 kept_cap, half_cap, lb_words;
+};
+
+Layout make_layout(i64 M, i64 T)
+{
+    const i64 N = M + T;
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](i64 bytes) {
+        const size_t o = off;
+        off = align_up(off + (size_t)std::max<i64>(bytes, 0));
+        return o;
+    };
+    L.ctrl = take(sizeof(Ctrl));
+    L.keysA = take(M * 4);
+    L.keysB = take(M * 4);
+    L.valsA = take(M * 4);
+    L.valsB = take(M * 4);
+    L.perm = take(M * 4);
+    L.ab0 = take(M * 8);
+    const i64 os_words = onesweep_tiles(M) * RADIX;
+    const i64 lv_words = level_tiles(N) + 1 + level_tiles(M) + 1;
+    L.lb_words = std::max(os_words, lv_words);
+    L.lb = take(L.lb_words * 8);
+    L.min_inc = take(N * 4);
+    L.ptr = take(N * 4);
+    L.vmap0 = take(N * 4);
+    // vertices of all levels >= 1: n_l = m_l + T and sum_{l>=1} m_l <= M
+    L.kept_cap = M + (i64)MAX_LEVELS * T + 64;
+    L.kept_ck = take(L.kept_cap * 4);
+    L.kept_vmap = take(L.kept_cap * 4);
+    // edges of levels >= 1 (ping-pong): m_1 <= M / 2 and m_{l+1} <= m_l / 2
+    L.half_cap = M / 2 + 1;
+    L.abX = take(L.half_cap * 8);
+    L.erX = take(L.half_cap * 4);
+    L.abY = take(L.half_cap * 8);
+    L.erY = take(L.half_cap * 4);
+    L.lev = take(M);
+    L.start = take(M * 4);
+    L.total = off + 256;   // slack for aligning an unaligned base
+    return L;
+}
+
+#define PANDORA_CUDA(call)                 \
+    do {                                   \
+        if ((call) != cudaSuccess)         \
+            return PANDORA_ERR_CUDA;       \
+    } while (0)
+
+struct HostCounters {
+    int status;
+    int pad0;
+    u64 count_roots;
+    u64 count_alpha;
+};
+
+int read_counters(const Ctrl *ctrl, HostCounters *h, cudaStream_t s)
+{
+    PANDORA_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(HostCounters), cudaMemcpyDeviceToHost, s));
+    PANDORA_CUDA(cudaStreamSynchronize(s));
+    return PANDORA_OK;
+}
+
+// Passes of an 8-bit LSD sort that actually move keys (a pass whose digit is
+// the same for every key is the identity and is skipped).
+std::vector<int> useful_passes(const u32 (*hist)[RADIX], int n_passes, i64 m)
+{
+    std::vector<int> out;
+    for (int p = 0; p < n_passes; ++p) {
+        bool trivial = false;
+        for (int d = 0; d < RADIX; ++d)
+            if ((i64)hist[p][d] == m)
+                trivial = true;
+        if (!trivial)
+            out.push_back(p);
+    }
+    return out;
+}
+
+int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off, i32 *ep,
+        i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s)
+{
+    const i64 N = M + T;
+    if (stats)
+        std::memset(stats, 0, sizeof(*stats));
+    const Layout L = make_layout(M, T);
+    if (!ws || ws_bytes < L.total)
+        return PANDORA_ERR_WORKSPACE_TOO_SMALL;
+    char *base = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    Ctrl *ctrl = (Ctrl *)(base + L.ctrl);
+    u32 *keysA = (u32 *)(base + L.keysA), *keysB = (u32 *)(base + L.keysB);
+    u32 *valsA = (u32 *)(base + L.valsA), *valsB = (u32 *)(base + L.valsB);
+    u32 *perm = (u32 *)(base + L.perm);
+    int2 *ab0 = (int2 *)(base + L.ab0);
+    u64 *lb = (u64 *)(base + L.lb);
+    u32 *min_inc = (u32 *)(base + L.min_inc);
+    i32 *ptr = (i32 *)(base + L.ptr);
+    i32 *vmap0 = (i32 *)(base + L.vmap0);
+    u32 *kept_ck = (u32 *)(base + L.kept_ck);
+    i32 *kept_vmap = (i32 *)(base + L.kept_vmap);
+    int2 *abX = (int2 *)(base + L.abX), *abY = (int2 *)(base + L.abY);
+    u32 *erX = (u32 *)(base + L.erX), *erY = (u32 *)(base + L.erY);
+    unsigned char *lev = (unsigned char *)(base + L.lev);
+    i32 *start = (i32 *)(base + L.start);
+    int *status = &ctrl->status;
+
+    CallTimer timer(s);
+    PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    if (d_off)
+        timer.launch(K_CHECK_OFFSETS, T + 1, [&] { launch_check_offsets(d_off, T, M, status, s); });
+    HostCounters h{};
+    if (M == 0) {
+        timer.launch(K_FILL, N, [&] { launch_fill(vp, N, -1, s); });
+        PANDORA_CUDA(cudaGetLastError());
+        if (int e = read_counters(ctrl, &h, s))
+            return e;
+        return h.status;
+    }
+
+    // ---- 1. sort by (weight, index) -------------------------------------------
+    timer.launch(K_HIST_WEIGHTS, M, [&] { launch_hist_weights(w, M, &ctrl->hist1[0][0], status, s); });
+    static thread_local u32 hhist[4][RADIX];
+    PANDORA_CUDA(cudaMemcpyAsync(hhist, ctrl->hist1, sizeof(hhist), cudaMemcpyDeviceToHost, s));
+    if (int e = read_counters(ctrl, &h, s))
+        return e;
+    if (h.status)
+        return h.status;
+    std::vector<int> passes = useful_passes(hhist, 4, M);
+    if (passes.empty())
+        passes.push_back(3);   // still one pass: it writes the permutation and endpoints
+    const u32 *cur_k = nullptr, *cur_v = nullptr;
+    bool toA = false;
+    for (size_t k = 0; k < passes.size(); ++k) {
+        const bool first = k == 0, last = k + 1 == passes.size();
+        OnesweepParams P{};
+        P.n = M;
+        P.shift = 8 * passes[k];
+        P.hist = ctrl->hist1[passes[k]];
+        P.lb = lb;
+        P.tile_counter = &ctrl->tile_counter[0];
+        P.status = status;
+        int flags = 0;
+        if (first) {
+            flags |= OS_KEY_FROM_W | OS_GEN_VALS;
+            P.w_in = w;
+        } else {
+            P.keys_in = cur_k;
+            P.vals_in = cur_v;
+        }
+        if (last) {
+            flags |= OS_GATHER | (d_off ? OS_FOREST : 0);
+            P.vals_out = perm;
+            P.u = u;
+            P.v = v;
+            P.ab_out = ab0;
+            P.n_vertices = N;
+            P.edge_off = d_off;
+            P.n_trees = T;
+        } else {
+            flags |= OS_WRITE_KEYS;
+            P.keys_out = toA ? keysA : keysB;
+            P.vals_out = toA ? valsA : valsB;
+        }
+        PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
+        timer.launch(K_SORT_WEIGHTS, M, [&] { launch_onesweep(flags, P, s); });
+        cur_k = P.keys_out;
+        cur_v = P.vals_out;
+        toA = !toA;
+    }
+    PANDORA_CUDA(cudaGetLastError());
+
+    // ---- 2. contraction levels ------------------------------------------------
+    const int2 *ab = ab0;
+    const u32 *er = nullptr;
+    i64 m_l = M, n_l = N, kept_used = 0;
+    LevelTable table{};
+    int n_levels = 0;
+    bool useX = true;
+    for (int l = 0;; ++l) {
+        if (l >= MAX_LEVELS)
+            return PANDORA_ERR_ITERATION_LIMIT;
+        LevelParams P{};
+        P.level = l;
+        P.m = m_l;
+        P.n = n_l;
+        P.ab = ab;
+        P.er = er;
+        P.min_inc = min_inc;
+        P.ptr = ptr;
+        if (l == 0) {
+            P.vmap = vmap0;
+            P.ck = nullptr;
+            P.perm = perm;
+            P.vertex_parent = vp;
+        } else {
+            if (kept_used + n_l > L.kept_cap)
+                return PANDORA_ERR_NOT_A_TREE;
+            P.vmap = kept_vmap + kept_used;
+            P.ck = kept_ck + kept_used;
+            kept_used += n_l;
+            table.ck[l] = P.ck;
+            table.vmap[l] = P.vmap;
+        }
+        P.edge_off = d_off;
+        P.n_trees = T;
+        P.ab_next = useX ? abX : abY;
+        P.er_next = useX ? erX : erY;
+        P.cap_next = L.half_cap;
+        P.lev = lev;
+        P.start = start;
+        P.lb = lb;
+        P.tile_counter = ctrl->tile_counter;
+        P.count_roots = &ctrl->count_roots;
+        P.count_alpha = &ctrl->count_alpha;
+        P.status = status;
+        PANDORA_CUDA(cudaMemsetAsync(min_inc, 0xFF, (size_t)n_l * 4, s));
+        PANDORA_CUDA(cudaMemsetAsync(
+            lb, 0, (size_t)(level_tiles(n_l) + 1 + level_tiles(m_l) + 1) * 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(&ctrl->count_roots, 0, 16, s));
+        timer.launch(K_MARK, m_l, [&] { launch_mark(P, s); });
+        timer.launch(K_PTR_INIT, n_l, [&] { launch_ptr_init(P, s); });
+        timer.launch(K_COMPRESS, n_l, [&] { launch_compress(P, s); });
+        timer.launch(K_COMPACT, m_l, [&] { launch_compact(P, s); });
+        PANDORA_CUDA(cudaGetLastError());
+        if (int e = read_counters(ctrl, &h, s))
+            return e;
+        if (stats) {
+            stats->level_edges[l] = m_l;
+            stats->level_vertices[l] = n_l;
+            stats->n_levels = l + 1;
+        }
+        if (h.status)
+            return h.status;
+        n_levels = l + 1;
+        // every level of a forest of T trees has n_l = m_l + T
+        if ((i64)h.count_roots != (i64)h.count_alpha + T)
+            return PANDORA_ERR_NOT_A_TREE;
+        if (h.count_alpha == 0)
+            break;
+        if ((i64)h.count_alpha > L.half_cap)
+            return PANDORA_ERR_NOT_A_TREE;
+        ab = P.ab_next;
+        er = P.er_next;
+        m_l = (i64)h.count_alpha;
+        n_l = (i64)h.count_roots;
+        useX = !useX;
+    }
+
+    // ---- 3. expansion: chain key of every edge -----------------------------
+    const u32 root_base = (u32)(2 * M);
+    ExpandParams E{};
+    E.m = M;
+    E.n_levels = n_levels;
+    E.lev = lev;
+    E.start = start;
+    E.perm = perm;
+    E.keys_out = keysA;
+    E.root_base = root_base;
+    E.edge_off = d_off;
+    E.n_trees = T;
+    E.hist = &ctrl->hist2[0][0];
+    E.status = status;
+    timer.launch(K_EXPAND, M, [&] { launch_expand(E, table, s); });
+    PANDORA_CUDA(cudaGetLastError());
+    PANDORA_CUDA(cudaMemcpyAsync(hhist, ctrl->hist2, sizeof(hhist), cudaMemcpyDeviceToHost, s));
+    if (int e = read_counters(ctrl, &h, s))
+        return e;
+    if (h.status)
+        return h.status;
+
+    // ---- 4. stable sort by chain key, then link -------------------------------
+    const u64 max_key = (u64)root_base + (u64)T - 1;
+    int bits = 0;
+    while (bits < 32 && (max_key >> bits) != 0)
+        ++bits;
+    const std::vector<int> passes2 = useful_passes(hhist, (bits + 7) / 8, M);
+    const u32 *sk = keysA, *sv = perm;
+    for (size_t k = 0; k < passes2.size(); ++k) {
+        OnesweepParams P{};
+        P.n = M;
+        P.shift = 8 * passes2[k];
+        P.hist = ctrl->hist2[passes2[k]];
+        P.lb = lb;
+        P.tile_counter = &ctrl->tile_counter[0];
+        P.status = status;
+        P.keys_in = sk;
+        P.vals_in = sv;
+        const bool outB = (sk == keysA);
+        P.keys_out = outB ? keysB : keysA;
+        P.vals_out = outB ? valsB : valsA;
+        PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
+        timer.launch(K_SORT_CHAINS, M, [&] { launch_onesweep(OS_WRITE_KEYS, P, s); });
+        sk = P.keys_out;
+        sv = P.vals_out;
+    }
+    LinkParams K{};
+    K.m = M;
+    K.skeys = sk;
+    K.svals = sv;
+    K.perm = perm;
+    K.root_base = root_base;
+    K.edge_parent = ep;
+    K.edge_off = d_off;
+    K.n_trees = T;
+    timer.launch(K_LINK, M, [&] { launch_link(K, s); });
+    PANDORA_CUDA(cudaGetLastError());
+    if (int e = read_counters(ctrl, &h, s))
+        return e;
+    return h.status;
+}
+
+int check_common(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, i32 *ep, i32 *vp)
+{
+    if (M < 0 || T < 0)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (M + T > (i64)INT32_MAX)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (M > 0 && (!u || !v || !w || !ep))
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (M + T > 0 && !vp)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    return PANDORA_OK;
+}
+
+cudaMemPool_t library_pool(int dev)
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end())
+        return it->second;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess)
+        return nullptr;
+    u64 threshold = ~0ull;   // keep freed blocks for the next call
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    pools[dev] = pool;
+    return pool;
+}
+
+int run_pooled(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off,
+               i32 *ep, i32 *vp, cudaStream_t s)
+{
+    int dev = 0;
+    PANDORA_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = library_pool(dev);
+    if (!pool)
+        return PANDORA_ERR_CUDA;
+    const size_t bytes = make_layout(M, T).total;
+    void *ws = nullptr;
+    if (cudaMallocFromPoolAsync(&ws, bytes, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PANDORA_ERR_OUT_OF_MEMORY;
+    }
+    const int st = run(u, v, w, M, T, d_off, ep, vp, ws, bytes, nullptr, s);
+    cudaFreeAsync(ws, s);
+    if (st != PANDORA_OK)
+        cudaStreamSynchronize(s);
+    return st;
+}
+
+}  // namespace
+}  // namespace pandora
+
+using namespace pandora;
+
+extern "C" {
+
+int pandora_workspace_size(int64_t total_edges, int64_t n_trees, size_t *bytes)
+{
+    if (!bytes || total_edges < 0 || n_trees < 1 || total_edges + n_trees > (i64)INT32_MAX)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    *bytes = make_layout(total_edges, n_trees).total;
+    return PANDORA_OK;
+}
+
+int pandora_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                       int32_t *edge_parent, int32_t *vertex_parent, void *stream)
+{
+    if (int e = check_common(u, v, w, n_edges, 1, edge_parent, vertex_parent))
+        return e;
+    return run_pooled(u, v, w, n_edges, 1, nullptr, edge_parent, vertex_parent,
+                      (cudaStream_t)stream);
+}
+
+int pandora_dendrogram_ws(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                          int32_t *edge_parent, int32_t *vertex_parent, void *workspace,
+                          size_t workspace_bytes, pandora_stats *stats, void *stream)
+{
+    if (int e = check_common(u, v, w, n_edges, 1, edge_parent, vertex_parent))
+        return e;
+    return run(u, v, w, n_edges, 1, nullptr, edge_parent, vertex_parent, workspace,
+               workspace_bytes, stats, (cudaStream_t)stream);
+}
+
+int pandora_dendrogram_batched(const int32_t *u, const int32_t *v, const float *w,
+                               const int64_t *edge_offsets, int64_t n_trees, int64_t total_edges,
+                               int32_t *edge_parent, int32_t *vertex_parent, void *stream)
+{
+    if (int e = check_common(u, v, w, total_edges, n_trees, edge_parent, vertex_parent))
+        return e;
+    if (n_trees == 0)
+        return total_edges == 0 ? PANDORA_OK : PANDORA_ERR_INVALID_ARGUMENT;
+    if (!edge_offsets)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    return run_pooled(u, v, w, total_edges, n_trees, edge_offsets, edge_parent, vertex_parent,
+                      (cudaStream_t)stream);
+}
+
+int pandora_dendrogram_batched_ws(const int32_t *u, const int32_t *v, const float *w,
+                                  const int64_t *edge_offsets, int64_t n_trees,
+                                  int64_t total_edges, int32_t *edge_parent,
+                                  int32_t *vertex_parent, void *workspace,
+                                  size_t workspace_bytes, pandora_stats *stats, void *stream)
+{
+    if (int e = check_common(u, v, w, total_edges, n_trees, edge_parent, vertex_parent))
+        return e;
+    if (n_trees == 0)
+        return total_edges == 0 ? PANDORA_OK : PANDORA_ERR_INVALID_ARGUMENT;
+    if (!edge_offsets)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    return run(u, v, w, total_edges, n_trees, edge_offsets, edge_parent, vertex_parent,
+               workspace, workspace_bytes, stats, (cudaStream_t)stream);
+}
+
+int pandora_profile_start(int with_timing)
+{
+    Profiler &p = profiler();
+    std::lock_guard<std::mutex> lock(p.mu);
+    p.timing = with_timing != 0;
+    for (int k = 0; k < K_SLOTS; ++k) {
+        p.launches[k] = 0;
+        p.elements[k] = 0;
+        p.ms[k] = 0.0;
+    }
+    return PANDORA_OK;
+}
+
+int pandora_profile_read(pandora_profile *out)
+{
+    if (!out)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    std::memset(out, 0, sizeof(*out));
+    Profiler &p = profiler();
+    std::lock_guard<std::mutex> lock(p.mu);
+    out->n_kernels = K_SLOTS;
+    out->timing = p.timing ? 1 : 0;
+    for (int k = 0; k < K_SLOTS; ++k) {
+        std::strncpy(out->name[k], kSlotNames[k], sizeof(out->name[k]) - 1);
+        out->launches[k] = p.launches[k];
+        out->elements[k] = p.elements[k];
+        out->total_ms[k] = p.timing ? p.ms[k] : -1.0;
+    }
+    return PANDORA_OK;
+}
+
+const char *pandora_status_string(int status)
+{
+    switch (status) {
+    case PANDORA_OK: return "ok";
+    case PANDORA_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case PANDORA_ERR_NAN_WEIGHT: return "NaN weight";
+    case PANDORA_ERR_VERTEX_OUT_OF_RANGE: return "vertex id out of range";
+    case PANDORA_ERR_SELF_LOOP: return "self-loop edge";
+    case PANDORA_ERR_NOT_A_TREE: return "input is not a tree (cycle / disconnected)";
+    case PANDORA_ERR_ITERATION_LIMIT: return "device iteration limit reached";
+    case PANDORA_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PANDORA_ERR_CUDA: return "CUDA runtime error";
+    case PANDORA_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    default: return "unknown status";
+    }
+}
+
+int pandora_version(void) { return 100; }
+
+}  // extern "C"
