@@ -63,7 +63,8 @@ typedef enum pandora_status {
                                            on valid input) */
     PANDORA_ERR_OUT_OF_MEMORY = 7,      /* scratch allocation failed */
     PANDORA_ERR_CUDA = 8,               /* a CUDA runtime call failed */
-    PANDORA_ERR_WORKSPACE_TOO_SMALL = 9 /* caller workspace below pandora_workspace_size() */
+    PANDORA_ERR_WORKSPACE_TOO_SMALL = 9,/* caller workspace below pandora_workspace_size() */
+    PANDORA_ERR_SIZE_LIMIT = 10         /* n_edges above PANDORA_NOALLOC_MAX_EDGES */
 } pandora_status;
 
 /* Per-call statistics (optional output of the *_ws entry points). */
@@ -133,6 +134,32 @@ int pandora_dendrogram_batched_ws(const int32_t *u, const int32_t *v, const floa
                                   int64_t total_edges, int32_t *edge_parent,
                                   int32_t *vertex_parent, void *workspace,
                                   size_t workspace_bytes, pandora_stats *stats, void *stream);
+
+/*
+ * Allocation-free variant of pandora_dendrogram.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the time of the call -- for example code whose device
+ * memory is entirely owned by another allocator (a framework that reserved
+ * the GPU up front), or a latency-critical loop in which cudaMalloc/cudaFree
+ * would synchronise the device.  It takes the same arguments and gives the
+ * same result as pandora_dendrogram, but its scratch memory is a fixed
+ * 20 MiB array in the library's device image (held by every GPU that loads
+ * the library until the process exits), so it accepts at most
+ * PANDORA_NOALLOC_MAX_EDGES edges and returns PANDORA_ERR_SIZE_LIMIT above
+ * that.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The first call on a device looks up the device address of the array on
+ * that device (cudaGetSymbolAddress, with the device current); make that
+ * first call before any stream capture.  Every call reuses the same array
+ * and leaves its contents behind; each call clears what it needs zeroed, but
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on the array and must be serialised by the caller.  Blocking, like
+ * pandora_dendrogram.
+ */
+#define PANDORA_NOALLOC_MAX_EDGES 262143
+int pandora_dendrogram_noalloc(const int32_t *u, const int32_t *v, const float *w,
+                               int64_t n_edges, int32_t *edge_parent, int32_t *vertex_parent,
+                               void *stream);
 
 /*
  * Optional instrumentation (process-wide, thread-safe, host memory).

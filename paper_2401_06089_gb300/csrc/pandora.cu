@@ -496,6 +496,18 @@ int run_pooled(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i
 }
 
 }  // namespace
+
+// Entry for other translation units of the library (the allocation-free
+// entry point): the same pipeline on a workspace the caller of this function
+// provides.
+int run_on_workspace(const i32 *u, const i32 *v, const float *w, i64 M, i32 *ep, i32 *vp,
+                     void *ws, size_t ws_bytes, cudaStream_t s)
+{
+    return run(u, v, w, M, 1, nullptr, ep, vp, ws, ws_bytes, nullptr, s);
+}
+
+size_t workspace_bytes(i64 M, i64 T) { return make_layout(M, T).total; }
+
 }  // namespace pandora
 
 using namespace pandora;
@@ -603,6 +615,7 @@ const char *pandora_status_string(int status)
     case PANDORA_ERR_OUT_OF_MEMORY: return "out of device memory";
     case PANDORA_ERR_CUDA: return "CUDA runtime error";
     case PANDORA_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case PANDORA_ERR_SIZE_LIMIT: return "input larger than the static scratch of pandora_dendrogram_noalloc";
     default: return "unknown status";
     }
 }
