@@ -53,7 +53,7 @@ class Profile(ctypes.Structure):
 
 
 def library_path() -> str:
-    return os.path.join(HERE, _LIB_NAME)
+    return os.environ.get("PANDORA_LIBRARY") or os.path.join(HERE, _LIB_NAME)
 
 
 def load_library():

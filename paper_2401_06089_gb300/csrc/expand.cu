@@ -37,12 +37,13 @@ __global__ void __launch_bounds__(256) expand_kernel(const ExpandParams p, const
             i32 sv = p.start[r];
             key = NONE;
             for (int l = l0 + 1; l < p.n_levels; ++l) {
-                const u32 c = __ldg(t.ck[l] + sv);
+                const int2 rec = __ldg(t.rec[l] + sv);
+                const u32 c = (u32)rec.x;
                 if ((u32)r < (c >> 1)) {   // an isolated supervertex (c = NONE) ends here too
                     key = c;
                     break;
                 }
-                sv = __ldg(t.vmap[l] + sv);
+                sv = rec.y;
             }
             if (key == NONE) {
                 u32 tree = 0;

@@ -9,18 +9,29 @@ namespace pandora {
 // ---------------------------------------------------------------------------
 // sort.cu - onesweep LSD radix sort (8-bit digits, decoupled look-back)
 // ---------------------------------------------------------------------------
-constexpr int OS_THREADS = 256;
-constexpr int OS_ITEMS = 16;
+#ifndef PANDORA_OS_THREADS
+#define PANDORA_OS_THREADS 512
+#endif
+#ifndef PANDORA_OS_ITEMS
+#define PANDORA_OS_ITEMS 8
+#endif
+#ifndef PANDORA_OS_MIN_BLOCKS
+#define PANDORA_OS_MIN_BLOCKS 2
+#endif
+constexpr int OS_THREADS = PANDORA_OS_THREADS;
+constexpr int OS_ITEMS = PANDORA_OS_ITEMS;
+constexpr int OS_MIN_BLOCKS = PANDORA_OS_MIN_BLOCKS;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 constexpr int RADIX = 256;
 
 enum OnesweepFlags : int {
     OS_KEY_FROM_W = 1,    // keys are weight_key(w[i]) computed on the fly
-    OS_GEN_VALS = 2,      // values are the input positions (caller edge index)
+    OS_GEN_VALS = 2,      // value stream 0 is the input position (caller edge index);
+                          // with OS_PAYLOAD_UV the endpoints come from the caller's u, v
     OS_WRITE_KEYS = 4,    // write the sorted keys
-    OS_GATHER = 8,        // write (u, v) of the value's edge beside it (last pass of
-                          // the weight sort), validating the endpoints
-    OS_FOREST = 16,       // endpoints are tree-local (batched mode)
+    OS_PAYLOAD_UV = 8,    // carry the endpoints (u, v) as value streams 1 and 2
+    OS_LAST_AB = 16,      // write (u, v) as one int2 per edge (last weight pass)
+    OS_FOREST = 32,       // endpoints are tree-local (batched mode, first pass)
 };
 
 struct OnesweepParams {
@@ -29,13 +40,17 @@ struct OnesweepParams {
     const u32 *vals_in;
     u32 *keys_out;
     u32 *vals_out;
+    const u32 *pu_in;      // carried endpoints (OS_PAYLOAD_UV, later passes)
+    const u32 *pv_in;
+    u32 *pu_out;
+    u32 *pv_out;
     i64 n;
     int shift;
     const u32 *hist;       // [256] digit counts of this pass
     u64 *lb;               // [tiles * 256] look-back words, zeroed
     u32 *tile_counter;     // zeroed
     int *status;
-    // OS_GATHER
+    // caller endpoints (first pass) and level-0 output (last pass)
     const i32 *u;
     const i32 *v;
     int2 *ab_out;
@@ -59,16 +74,25 @@ constexpr int LV_TILE = LV_THREADS * LV_ITEMS;
 
 __host__ __device__ inline i64 level_tiles(i64 n) { return (n + LV_TILE - 1) / LV_TILE; }
 
+// Lightest-incident-edge word of a vertex x on one level (Eq. 1):
+//   bits 63..32  global rank r of the edge (ascending order of Section 3.1)
+//   bits 31..1   the edge's other endpoint y
+//   bit  0       side: 1 when x is the edge's second endpoint
+// The minimum over x's edges is the lightest edge, and the word carries what
+// the pointer forest and the chain key need without another gather.
+constexpr u64 NO_EDGE = ~0ull;
+
 struct LevelParams {
     int level;
     i64 m;                 // edges of this level
     i64 n;                 // vertices of this level
     const int2 *ab;        // endpoints (level vertex ids), ascending rank
     const u32 *er;         // global rank of each edge (nullptr on level 0: rank = index)
-    u32 *min_inc;          // [n] local index of the lightest incident edge
+    u64 *min_word;         // [n] lightest-incident-edge word (see above)
+    unsigned char *maybe;  // [m] bit s: the edge may be the lightest at endpoint s
     i32 *ptr;              // [n] pointer forest scratch
-    i32 *vmap;             // [n] vertex -> supervertex of the next level
-    u32 *ck;               // [n] chain key 2*rank(P(x)) + side (levels >= 1), or nullptr
+    i32 *vmap;             // [n] vertex -> supervertex (level 0)
+    int2 *rec;             // [n] {chain key, supervertex} kept for the expansion (levels >= 1)
     // level 0 only: vertex_parent output
     const u32 *perm;
     i32 *vertex_parent;
@@ -96,8 +120,7 @@ void launch_compact(const LevelParams &p, cudaStream_t s);
 // expand.cu - multilevel expansion (Section 3.3.2) and chain linking (3.3.3)
 // ---------------------------------------------------------------------------
 struct LevelTable {
-    const u32 *ck[MAX_LEVELS];
-    const i32 *vmap[MAX_LEVELS];
+    const int2 *rec[MAX_LEVELS];   // {chain key, supervertex} of every vertex of level l >= 1
 };
 
 struct ExpandParams {

@@ -4,20 +4,23 @@
 // listed in ascending global rank with endpoints given as level vertex ids.
 // Four kernels process it:
 //
-//   mark      min_inc[x] = local index of the lightest edge at x  (Eq. 1)
+//   mark      min_word[x] = (rank, other end, side) of the lightest edge at
+//             x (Eq. 1), by 64-bit atomicMin; the value each atomic returns
+//             tells whether the edge can still be the lightest there
 //   ptr_init  pointer forest: x points across its lightest edge; the two
 //             endpoints of a leaf edge (lightest at both, Section 3.1) point
 //             at each other and the smaller id becomes the root.  Roots get
 //             dense ids (a single-pass scan) that name the supervertices of
-//             the next level.  Also records the chain key of x (levels >= 1)
-//             and, on level 0, the vertex parents (Eq. 1).
-//   compress  root finding with path halving: vmap[x] = supervertex of x.
+//             the next level.  On level 0 it also writes the vertex parents
+//             (Eq. 1).
+//   compress  root finding with path halving: supervertex of x, packed on
+//             levels >= 1 with x's chain key for the expansion.
 //   compact   alpha-edges (Eq. 2: lightest at neither endpoint) are copied,
 //             in rank order, to the next level with relabelled endpoints;
 //             every other edge is contracted here and records the level and
 //             its supervertex for the expansion.
 //
-// The non-alpha edges are exactly the edges {min_inc[x]}, so the components
+// The non-alpha edges are exactly the lightest edges {P(x)}, so the components
 // of the pointer forest are the components the paper contracts.  Along a
 // pointer path the edge ranks strictly decrease except across a leaf edge,
 // hence the forest is acyclic once each leaf edge's 2-cycle is broken.
@@ -78,21 +81,29 @@ __device__ __forceinline__ void tile_rank(const bool (&flag)[LV_ITEMS], u32 (&ra
     *tile_total = s_total;
 }
 
-__global__ void __launch_bounds__(256) mark_kernel(const int2 *__restrict__ ab, i64 m,
-                                                   u32 *__restrict__ min_inc)
+template <bool LEVEL0>
+__global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m)
+    if (i >= p.m)
         return;
-    const int2 e = ab[i];
-    const u32 r = (u32)i;
-    // Filtering by a plain read first keeps hub vertices (stars) from
-    // serialising on one address: min_inc only decreases, so a stale read can
-    // cause an unneeded atomic but never a wrong skip.
-    if (min_inc[e.x] > r)
-        atomicMin(min_inc + e.x, r);
-    if (min_inc[e.y] > r)
-        atomicMin(min_inc + e.y, r);
+    const int2 e = p.ab[i];
+    const u64 r = LEVEL0 ? (u64)i : (u64)p.er[i];
+    const u64 wa = (r << 32) | ((u64)(u32)e.y << 1);        // at e.x: other end e.y, side 0
+    const u64 wb = (r << 32) | ((u64)(u32)e.x << 1) | 1u;   // at e.y: other end e.x, side 1
+    // A plain read first keeps hub vertices (stars) from serialising on one
+    // address: the word only decreases, so a stale read may cost an unneeded
+    // atomic but never a wrong skip.  The value seen (old) decides whether
+    // this edge can still be the lightest at that endpoint.
+    u64 old = p.min_word[e.x];
+    if (old > wa)
+        old = atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
+    const bool maybe_a = old > wa;
+    old = p.min_word[e.y];
+    if (old > wb)
+        old = atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
+    const bool maybe_b = old > wb;
+    p.maybe[i] = (unsigned char)((maybe_a ? 1 : 0) | (maybe_b ? 2 : 0));
 }
 
 template <bool LEVEL0, bool FOREST>
@@ -113,36 +124,30 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
         nxt[it] = (i32)x;
         if (x >= p.n)
             continue;
-        const u32 i = p.min_inc[x];
-        u32 ck = NONE;
-        if (i == NONE) {
-            root[it] = true;   // isolated vertex: a finished tree of a forest, or n = 1
+        const u64 wx = p.min_word[x];
+        if (wx == NO_EDGE) {
+            root[it] = true;   // isolated vertex: a finished tree of a forest
         } else {
-            const int2 e = __ldg(p.ab + i);
-            const i32 y = e.x ^ e.y ^ (i32)x;
+            const u32 r = (u32)(wx >> 32);
+            const i32 y = (i32)((wx >> 1) & 0x7FFFFFFFu);
             if (y == (i32)x) {
                 root[it] = true;   // self-loop: reported by compact on the level above
             } else {
-                const u32 j = p.min_inc[y];
-                root[it] = (j == i) && ((i32)x < y);
+                // a leaf edge (lightest at both ends) closes a 2-cycle; its
+                // smaller endpoint becomes the root of the component
+                const u64 wy = p.min_word[y];
+                root[it] = ((u32)(wy >> 32) == r) && ((i32)x < y);
                 nxt[it] = y;
             }
-            if (!LEVEL0) {
-                const u32 r = __ldg(p.er + i);
-                ck = 2u * r + (e.y == (i32)x ? 1u : 0u);
-            }
-        }
-        if (!LEVEL0)
-            p.ck[x] = ck;
-        if (LEVEL0) {
-            i32 par = -1;
-            if (i != NONE) {
-                par = (i32)__ldg(p.perm + i);
+            if (LEVEL0) {
+                i32 par = (i32)__ldg(p.perm + r);   // Eq. 1, caller edge id
                 if (FOREST)
                     par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, par));
+                p.vertex_parent[x] = par;
             }
-            p.vertex_parent[x] = par;
         }
+        if (LEVEL0 && wx == NO_EDGE)
+            p.vertex_parent[x] = -1;
     }
     u32 rank[LV_ITEMS];
     u64 base;
@@ -158,12 +163,16 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
         *p.count_roots = base + total;
 }
 
-__global__ void __launch_bounds__(256) compress_kernel(i32 *ptr, i32 *__restrict__ vmap, i64 n,
-                                                       int *status)
+// Root finding with path halving.  Writes the supervertex of x; on levels
+// >= 1 also the chain key 2*rank(P(x)) + side that the expansion compares
+// against, packed with it.
+template <bool LEVEL0>
+__global__ void __launch_bounds__(256) compress_kernel(const LevelParams p)
 {
     const i64 x = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= n)
+    if (x >= p.n)
         return;
+    i32 *ptr = p.ptr;
     i32 cur = (i32)x;
     i32 res;
     i64 iter = 0;
@@ -180,13 +189,19 @@ __global__ void __launch_bounds__(256) compress_kernel(i32 *ptr, i32 *__restrict
         }
         st_volatile(ptr + cur, g);   // path halving: g is an ancestor of cur
         cur = g;
-        if (++iter > n + 64) {
-            set_status(status, PANDORA_ERR_ITERATION_LIMIT);
+        if (++iter > p.n + 64) {
+            set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
             res = ~0;
             break;
         }
     }
-    vmap[x] = ~res;
+    if (LEVEL0) {
+        p.vmap[x] = ~res;
+    } else {
+        const u64 wx = p.min_word[x];
+        const u32 ck = wx == NO_EDGE ? NONE : 2u * (u32)(wx >> 32) + (u32)(wx & 1u);
+        p.rec[x] = make_int2((i32)ck, ~res);
+    }
     if (cur != (i32)x)
         st_volatile(ptr + x, res);     // later walks through x stop here
 }
@@ -211,12 +226,14 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
             continue;
         const int2 e = p.ab[i];
         const u32 r = LEVEL0 ? (u32)i : p.er[i];
+        const unsigned mb = p.maybe[i];
         rr[it] = r;
-        const bool a_min = p.min_inc[e.x] == (u32)i;
-        const bool b_min = p.min_inc[e.y] == (u32)i;
-        const i32 va = p.vmap[e.x];
+        // Eq. 2: an alpha-edge is the lightest incident edge of neither endpoint
+        const bool a_min = (mb & 1) && (u32)(p.min_word[e.x] >> 32) == r;
+        const bool b_min = (mb & 2) && (u32)(p.min_word[e.y] >> 32) == r;
+        const i32 va = LEVEL0 ? p.vmap[e.x] : p.rec[e.x].y;
         if (!a_min && !b_min) {
-            const i32 vb = p.vmap[e.y];
+            const i32 vb = LEVEL0 ? p.vmap[e.y] : p.rec[e.y].y;
             if (va == vb)
                 set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // a cycle closed up
             alpha[it] = true;
@@ -253,7 +270,11 @@ void launch_mark(const LevelParams &p, cudaStream_t s)
 {
     if (p.m <= 0)
         return;
-    mark_kernel<<<(unsigned)((p.m + 255) / 256), 256, 0, s>>>(p.ab, p.m, p.min_inc);
+    const unsigned blocks = (unsigned)((p.m + 255) / 256);
+    if (p.level == 0)
+        mark_kernel<true><<<blocks, 256, 0, s>>>(p);
+    else
+        mark_kernel<false><<<blocks, 256, 0, s>>>(p);
 }
 
 void launch_ptr_init(const LevelParams &p, cudaStream_t s)
@@ -271,7 +292,11 @@ void launch_ptr_init(const LevelParams &p, cudaStream_t s)
 
 void launch_compress(const LevelParams &p, cudaStream_t s)
 {
-    compress_kernel<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p.ptr, p.vmap, p.n, p.status);
+    const unsigned blocks = (unsigned)((p.n + 255) / 256);
+    if (p.level == 0)
+        compress_kernel<true><<<blocks, 256, 0, s>>>(p);
+    else
+        compress_kernel<false><<<blocks, 256, 0, s>>>(p);
 }
 
 void launch_compact(const LevelParams &p, cudaStream_t s)

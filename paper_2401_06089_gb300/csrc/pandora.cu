@@ -124,8 +124,8 @@ class CallTimer {
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_inc, ptr, vmap0;
-    size_t kept_ck, kept_vmap, abX, erX, abY, erY, lev, start, total;
+    size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, maybe, ptr, vmap0;
+    size_t kept_rec, abX, erX, abY, erY, lev, start, total;
     i64 kept_cap, half_cap, lb_words;
 };
 
@@ -150,13 +150,13 @@ Layout make_layout(i64 M, i64 T)
     const i64 lv_words = level_tiles(N) + 1 + level_tiles(M) + 1;
     L.lb_words = std::max(os_words, lv_words);
     L.lb = take(L.lb_words * 8);
-    L.min_inc = take(N * 4);
+    L.min_word = take(N * 8);
+    L.maybe = take(M);
     L.ptr = take(N * 4);
     L.vmap0 = take(N * 4);
     // vertices of all levels >= 1: n_l = m_l + T and sum_{l>=1} m_l <= M
     L.kept_cap = M + (i64)MAX_LEVELS * T + 64;
-    L.kept_ck = take(L.kept_cap * 4);
-    L.kept_vmap = take(L.kept_cap * 4);
+    L.kept_rec = take(L.kept_cap * 8);
     // edges of levels >= 1 (ping-pong): m_1 <= M / 2 and m_{l+1} <= m_l / 2
     L.half_cap = M / 2 + 1;
     L.abX = take(L.half_cap * 8);
@@ -221,11 +221,11 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     u32 *perm = (u32 *)(base + L.perm);
     int2 *ab0 = (int2 *)(base + L.ab0);
     u64 *lb = (u64 *)(base + L.lb);
-    u32 *min_inc = (u32 *)(base + L.min_inc);
+    u64 *min_word = (u64 *)(base + L.min_word);
+    unsigned char *maybe = (unsigned char *)(base + L.maybe);
     i32 *ptr = (i32 *)(base + L.ptr);
     i32 *vmap0 = (i32 *)(base + L.vmap0);
-    u32 *kept_ck = (u32 *)(base + L.kept_ck);
-    i32 *kept_vmap = (i32 *)(base + L.kept_vmap);
+    int2 *kept_rec = (int2 *)(base + L.kept_rec);
     int2 *abX = (int2 *)(base + L.abX), *abY = (int2 *)(base + L.abY);
     u32 *erX = (u32 *)(base + L.erX), *erY = (u32 *)(base + L.erY);
     unsigned char *lev = (unsigned char *)(base + L.lev);
@@ -256,7 +256,12 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     std::vector<int> passes = useful_passes(hhist, 4, M);
     if (passes.empty())
         passes.push_back(3);   // still one pass: it writes the permutation and endpoints
-    const u32 *cur_k = nullptr, *cur_v = nullptr;
+    // the endpoint streams ping-pong through arrays that are idle until the
+    // level loop: the two halves of kept_rec (>= M entries each), min_word
+    // (2N entries) and ptr (N)
+    u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + L.kept_cap;
+    u32 *puB = (u32 *)min_word, *pvB = (u32 *)ptr;
+    const u32 *cur_k = nullptr, *cur_v = nullptr, *cur_u = nullptr, *cur_w = nullptr;
     bool toA = false;
     for (size_t k = 0; k < passes.size(); ++k) {
         const bool first = k == 0, last = k + 1 == passes.size();
@@ -267,33 +272,39 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         P.lb = lb;
         P.tile_counter = &ctrl->tile_counter[0];
         P.status = status;
-        int flags = 0;
+        P.u = u;
+        P.v = v;
+        P.n_vertices = N;
+        P.edge_off = d_off;
+        P.n_trees = T;
+        int flags = OS_PAYLOAD_UV;
         if (first) {
-            flags |= OS_KEY_FROM_W | OS_GEN_VALS;
+            flags |= OS_KEY_FROM_W | OS_GEN_VALS | (d_off ? OS_FOREST : 0);
             P.w_in = w;
         } else {
             P.keys_in = cur_k;
             P.vals_in = cur_v;
+            P.pu_in = cur_u;
+            P.pv_in = cur_w;
         }
         if (last) {
-            flags |= OS_GATHER | (d_off ? OS_FOREST : 0);
+            flags |= OS_LAST_AB;
             P.vals_out = perm;
-            P.u = u;
-            P.v = v;
             P.ab_out = ab0;
-            P.n_vertices = N;
-            P.edge_off = d_off;
-            P.n_trees = T;
         } else {
             flags |= OS_WRITE_KEYS;
             P.keys_out = toA ? keysA : keysB;
             P.vals_out = toA ? valsA : valsB;
+            P.pu_out = toA ? puA : puB;
+            P.pv_out = toA ? pvA : pvB;
         }
         PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
         timer.launch(K_SORT_WEIGHTS, M, [&] { launch_onesweep(flags, P, s); });
         cur_k = P.keys_out;
         cur_v = P.vals_out;
+        cur_u = P.pu_out;
+        cur_w = P.pv_out;
         toA = !toA;
     }
     PANDORA_CUDA(cudaGetLastError());
@@ -314,21 +325,19 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         P.n = n_l;
         P.ab = ab;
         P.er = er;
-        P.min_inc = min_inc;
+        P.min_word = min_word;
+        P.maybe = maybe;
         P.ptr = ptr;
         if (l == 0) {
             P.vmap = vmap0;
-            P.ck = nullptr;
             P.perm = perm;
             P.vertex_parent = vp;
         } else {
             if (kept_used + n_l > L.kept_cap)
                 return PANDORA_ERR_NOT_A_TREE;
-            P.vmap = kept_vmap + kept_used;
-            P.ck = kept_ck + kept_used;
+            P.rec = kept_rec + kept_used;
             kept_used += n_l;
-            table.ck[l] = P.ck;
-            table.vmap[l] = P.vmap;
+            table.rec[l] = P.rec;
         }
         P.edge_off = d_off;
         P.n_trees = T;
@@ -342,7 +351,7 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         P.count_roots = &ctrl->count_roots;
         P.count_alpha = &ctrl->count_alpha;
         P.status = status;
-        PANDORA_CUDA(cudaMemsetAsync(min_inc, 0xFF, (size_t)n_l * 4, s));
+        PANDORA_CUDA(cudaMemsetAsync(min_word, 0xFF, (size_t)n_l * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(
             lb, 0, (size_t)(level_tiles(n_l) + 1 + level_tiles(m_l) + 1) * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 8, s));

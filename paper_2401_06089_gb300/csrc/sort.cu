@@ -1,20 +1,26 @@
-// Onesweep LSD radix sort of (key, value) pairs for sm_103a.
+// Onesweep LSD radix sort of (key, value...) tuples for sm_103a.
 //
 // Paper step: the edges are sorted by weight with a consistent tie rule
 // (Section 3.1); the chains are sorted again after expansion (Section 3.3.3).
 // Both sorts are stable LSD radix sorts over 8-bit digits, so equal keys keep
-// their input order: for the weight sort the value is the caller edge index
-// and ties therefore resolve by index, for the chain sort the input is in
-// ascending rank so every chain comes out in ascending rank.
+// their input order: for the weight sort the first value stream is the
+// caller edge index and ties therefore resolve by index; for the chain sort
+// the input is in ascending rank, so every chain comes out in ascending rank.
 //
 // One pass = one kernel (Adinets & Merrill's onesweep): a block takes the
-// next tile id from an atomic counter, ranks its 4096 keys by digit with
-// warp ballots (stable: warp w of the tile owns a contiguous run of 512
-// keys, processed 32 at a time in order), publishes its per-digit counts and
-// finds the counts of all earlier tiles by decoupled look-back, then
-// scatters keys and values through shared memory so that each digit's run is
-// written contiguously.  The per-pass digit totals come from one histogram
-// read of all keys done before the first pass.
+// next tile id from an atomic counter, ranks its keys by digit with warp
+// ballots (stable: warp w of the tile owns a contiguous run of keys, taken 32
+// at a time in order), publishes its per-digit counts and sums the counts of
+// all earlier tiles by decoupled look-back (eight predecessor tiles per
+// round trip), then scatters keys and each value stream through shared
+// memory so that every digit's run is written contiguously.  The per-pass
+// digit totals come from one histogram read of all keys before the first
+// pass.
+//
+// The weight sort carries the endpoints (u, v) as two extra value streams:
+// moving 8 more bytes per edge through each pass is cheaper than gathering
+// them at random afterwards (a random 4-byte read costs a 64-byte DRAM
+// burst).
 #include "kernels.cuh"
 
 namespace pandora {
@@ -22,10 +28,12 @@ namespace pandora {
 namespace {
 
 constexpr int OS_WARPS = OS_THREADS / 32;
-static_assert(OS_THREADS == RADIX, "one thread per digit");
+constexpr int LB_BATCH = 8;
+static_assert(OS_THREADS >= RADIX, "one thread per digit");
 
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ __forceinline__ u32 block_exclusive_scan_256(u32 x, u32 *s_warp)
+// Exclusive scan of one value per thread over the first 256 threads of the
+// block (all threads must call; threads >= 256 pass 0 and get garbage).
+__device__ __forceinline__ u32 digit_exclusive_scan(u32 x, u32 *s_warp)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u32 incl = x;
@@ -35,12 +43,12 @@ __device__ __forceinline__ u32 block_exclusive_scan_256(u32 x, u32 *s_warp)
         if (lane >= off)
             incl += y;
     }
-    if (lane == 31)
+    if (lane == 31 && warp < RADIX / 32)
         s_warp[warp] = incl;
     __syncthreads();
     u32 prefix = 0;
 #pragma unroll
-    for (int k = 0; k < OS_WARPS; ++k)
+    for (int k = 0; k < RADIX / 32; ++k)
         prefix += (k < warp) ? s_warp[k] : 0u;
     __syncthreads();
     return prefix + incl - x;
@@ -89,13 +97,17 @@ __global__ void __launch_bounds__(256) hist_weights_kernel(const float *__restri
 }
 
 template <int FLAGS>
-__global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepParams p)
+__global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(const OnesweepParams p)
 {
+    constexpr bool kAB = (FLAGS & OS_LAST_AB) != 0;
+    constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;
     __shared__ u32 s_whist[OS_WARPS][RADIX];   // per-warp digit counts, then offsets
     __shared__ u32 s_buf[OS_TILE];             // tile in digit order (keys, then values)
+    __shared__ u32 s_buf2[kUV ? OS_TILE : 1];  // v beside u
     __shared__ u32 s_goff[RADIX];              // global position of local position 0, per digit
+    __shared__ unsigned char s_dig[OS_TILE];   // digit of each local position
     __shared__ u32 s_local_start[RADIX];
-    __shared__ u32 s_warp[OS_WARPS];
+    __shared__ u32 s_warp[RADIX / 32];
     __shared__ u32 s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -104,7 +116,7 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepPara
     if (tid == 0)
         s_tile = atomicAdd(p.tile_counter, 1u);
     // global start of every digit's bucket (exclusive scan of the pass histogram)
-    const u32 bin_base = block_exclusive_scan_256(p.hist[tid], s_warp);
+    const u32 bin_base = digit_exclusive_scan(tid < RADIX ? p.hist[tid] : 0u, s_warp);
     const u32 tile = s_tile;   // published before the scan's barriers
     const i64 tile_base = (i64)tile * OS_TILE;
     const i64 warp_base = tile_base + (i64)warp * (32 * OS_ITEMS);
@@ -115,14 +127,10 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepPara
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
         const i64 idx = warp_base + it * 32 + lane;
-        if (idx < p.n) {
-            if (FLAGS & OS_KEY_FROM_W)
-                reg[it] = weight_key(p.w_in[idx]);
-            else
-                reg[it] = p.keys_in[idx];
-        } else {
+        if (idx < p.n)
+            reg[it] = (FLAGS & OS_KEY_FROM_W) ? weight_key(p.w_in[idx]) : p.keys_in[idx];
+        else
             reg[it] = 0;
-        }
     }
 
     // ---- stable warp-level ranking by digit (ballot multisplit) ------------
@@ -153,16 +161,19 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepPara
 
     // ---- per-digit totals of the tile; publish for look-back ---------------
     u32 total = 0;
-#pragma unroll
-    for (int k = 0; k < OS_WARPS; ++k) {
-        const u32 c = s_whist[k][tid];
-        s_whist[k][tid] = total;
-        total += c;
-    }
     u64 *lbt = p.lb + (u64)tile * RADIX;
-    st_relaxed(lbt + tid, (tile == 0 ? LB_INC : LB_AGG) | (u64)total);
-    const u32 local_start = block_exclusive_scan_256(total, s_warp);
-    s_local_start[tid] = local_start;
+    if (tid < RADIX) {
+#pragma unroll
+        for (int k = 0; k < OS_WARPS; ++k) {
+            const u32 c = s_whist[k][tid];
+            s_whist[k][tid] = total;
+            total += c;
+        }
+        st_relaxed(lbt + tid, (tile == 0 ? LB_INC : LB_AGG) | (u64)total);
+    }
+    const u32 local_start = digit_exclusive_scan(total, s_warp);
+    if (tid < RADIX)
+        s_local_start[tid] = local_start;
     __syncthreads();
 
     // ---- keys into shared memory in digit order ----------------------------
@@ -176,56 +187,70 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepPara
             lpos[it] = pos;
         }
     }
-    // values into registers while the look-back runs
-#pragma unroll
-    for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        if (FLAGS & OS_GEN_VALS)
-            reg[it] = (u32)idx;
-        else
-            reg[it] = idx < p.n ? p.vals_in[idx] : 0u;
-    }
 
-    // ---- decoupled look-back, one thread per digit -------------------------
-    u64 excl = 0;
-    if (tile > 0) {
-        i64 j = (i64)tile - 1;
-        u32 spins = 0;
-        while (j >= 0) {
-            const u64 s = ld_relaxed(p.lb + (u64)j * RADIX + tid);
-            const u64 f = s & ~LB_VAL;
-            if (f == 0) {
-                if (++spins > SPIN_LIMIT) {
-                    set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
-                    break;
+    // ---- decoupled look-back, one thread per digit, 8 tiles per round trip --
+    if (tid < RADIX) {
+        u64 excl = 0;
+        if (tile > 0) {
+            i64 j = (i64)tile - 1;
+            u32 spins = 0;
+            for (;;) {
+                u64 s[LB_BATCH];
+#pragma unroll
+                for (int k = 0; k < LB_BATCH; ++k)
+                    s[k] = (j - k >= 0) ? ld_relaxed(p.lb + (u64)(j - k) * RADIX + tid) : LB_INC;
+                int consumed = 0;
+                bool done = false;
+#pragma unroll
+                for (int k = 0; k < LB_BATCH; ++k) {
+                    if (done || consumed < k)
+                        continue;
+                    const u64 f = s[k] & ~LB_VAL;
+                    if (f == 0)
+                        continue;            // not published yet: reload from here
+                    excl += s[k] & LB_VAL;
+                    consumed = k + 1;
+                    if (f == LB_INC)
+                        done = true;
                 }
-                if (spins > 32)
-                    __nanosleep(32);
-                continue;
+                if (done)
+                    break;
+                j -= consumed;
+                if (consumed == 0) {
+                    if (++spins > SPIN_LIMIT) {
+                        set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
+                        break;
+                    }
+                    if (spins > 16)
+                        __nanosleep(32);
+                }
             }
-            excl += s & LB_VAL;
-            if (f == LB_INC)
-                break;
-            --j;
+            st_relaxed(lbt + tid, LB_INC | (excl + total));
         }
-        st_relaxed(lbt + tid, LB_INC | (excl + total));
+        s_goff[tid] = bin_base + (u32)excl - local_start;   // modulo 2^32
     }
-    s_goff[tid] = bin_base + (u32)excl - local_start;   // modulo 2^32
     __syncthreads();
 
     // ---- write keys, one digit run after another ---------------------------
     const i64 rem = p.n - tile_base;
     const int tile_count = rem < OS_TILE ? (int)rem : OS_TILE;
-    u32 dj[OS_ITEMS];
 #pragma unroll
     for (int k = 0; k < OS_ITEMS; ++k) {
         const int j = k * OS_THREADS + tid;
         if (j < tile_count) {
             const u32 key = s_buf[j];
-            dj[k] = (key >> shift) & 255u;
+            const u32 d = (key >> shift) & 255u;
+            s_dig[j] = (unsigned char)d;
             if (FLAGS & OS_WRITE_KEYS)
-                p.keys_out[s_goff[dj[k]] + (u32)j] = key;
+                p.keys_out[s_goff[d] + (u32)j] = key;
         }
+    }
+
+    // ---- value stream 0: caller edge index --------------------------------------
+#pragma unroll
+    for (int it = 0; it < OS_ITEMS; ++it) {
+        const i64 idx = warp_base + it * 32 + lane;
+        reg[it] = idx < p.n ? ((FLAGS & OS_GEN_VALS) ? (u32)idx : p.vals_in[idx]) : 0u;
     }
     __syncthreads();
 #pragma unroll
@@ -235,34 +260,63 @@ __global__ void __launch_bounds__(OS_THREADS) onesweep_kernel(const OnesweepPara
             s_buf[lpos[it]] = reg[it];
     }
     __syncthreads();
-
-    // ---- write values (and, on the last weight pass, the endpoints) --------
 #pragma unroll
     for (int k = 0; k < OS_ITEMS; ++k) {
         const int j = k * OS_THREADS + tid;
-        if (j < tile_count) {
-            const u32 val = s_buf[j];
-            const u32 pos = s_goff[dj[k]] + (u32)j;
-            p.vals_out[pos] = val;
-            if (FLAGS & OS_GATHER) {
-                i32 a = __ldg(p.u + val);
-                i32 b = __ldg(p.v + val);
-                i64 nv = p.n_vertices;
-                i64 voff = 0;
-                if (FLAGS & OS_FOREST) {
-                    const i64 t = tree_of_edge(p.edge_off, p.n_trees, (i64)val);
-                    const i64 e0 = __ldg(p.edge_off + t), e1 = __ldg(p.edge_off + t + 1);
-                    nv = e1 - e0 + 1;
-                    voff = e0 + t;
+        if (j < tile_count)
+            p.vals_out[s_goff[s_dig[j]] + (u32)j] = s_buf[j];
+    }
+
+    // ---- value streams 1, 2: endpoints u, v -----------------------------------
+    if (FLAGS & OS_PAYLOAD_UV) {
+        __syncthreads();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            u32 *dst = half == 0 ? s_buf : s_buf2;
+#pragma unroll
+            for (int it = 0; it < OS_ITEMS; ++it) {
+                const i64 idx = warp_base + it * 32 + lane;
+                if (idx < p.n) {
+                    u32 x;
+                    if (FLAGS & OS_GEN_VALS) {
+                        // first pass: read the caller's endpoints, validate them and
+                        // turn tree-local ids into forest ids
+                        i32 a = p.u[idx], b = p.v[idx];
+                        i64 nv = p.n_vertices, voff = 0;
+                        if (FLAGS & OS_FOREST) {
+                            const i64 t = tree_of_edge(p.edge_off, p.n_trees, idx);
+                            const i64 e0 = __ldg(p.edge_off + t), e1 = __ldg(p.edge_off + t + 1);
+                            nv = e1 - e0 + 1;
+                            voff = e0 + t;
+                        }
+                        if (a < 0 || (i64)a >= nv || b < 0 || (i64)b >= nv) {
+                            if (half == 0)
+                                set_status(p.status, PANDORA_ERR_VERTEX_OUT_OF_RANGE);
+                            a = 0;
+                            b = 0;
+                        } else if (a == b && half == 0) {
+                            set_status(p.status, PANDORA_ERR_SELF_LOOP);
+                        }
+                        x = (u32)((half == 0 ? a : b) + voff);
+                    } else {
+                        x = half == 0 ? p.pu_in[idx] : p.pv_in[idx];
+                    }
+                    dst[lpos[it]] = x;
                 }
-                if (a < 0 || (i64)a >= nv || b < 0 || (i64)b >= nv) {
-                    set_status(p.status, PANDORA_ERR_VERTEX_OUT_OF_RANGE);
-                    a = 0;
-                    b = 0;
-                } else if (a == b) {
-                    set_status(p.status, PANDORA_ERR_SELF_LOOP);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < OS_ITEMS; ++k) {
+            const int j = k * OS_THREADS + tid;
+            if (j < tile_count) {
+                const u32 pos = s_goff[s_dig[j]] + (u32)j;
+                if (kAB) {
+                    p.ab_out[pos] = make_int2((i32)s_buf[j], (i32)s_buf2[j]);
+                } else {
+                    p.pu_out[pos] = s_buf[j];
+                    p.pv_out[pos] = s_buf2[j];
                 }
-                p.ab_out[pos] = make_int2((i32)(a + voff), (i32)(b + voff));
             }
         }
     }
@@ -291,14 +345,15 @@ void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s)
 {
     if (p.n <= 0)
         return;
+    constexpr int FIRST = OS_KEY_FROM_W | OS_GEN_VALS | OS_PAYLOAD_UV;
     switch (flags) {
-    // weight sort: first, middle, last pass and single pass (one or forest)
-    case OS_KEY_FROM_W | OS_GEN_VALS | OS_WRITE_KEYS: launch_os<OS_KEY_FROM_W | OS_GEN_VALS | OS_WRITE_KEYS>(p, s); break;
+    case FIRST | OS_WRITE_KEYS: launch_os<FIRST | OS_WRITE_KEYS>(p, s); break;
+    case FIRST | OS_WRITE_KEYS | OS_FOREST: launch_os<FIRST | OS_WRITE_KEYS | OS_FOREST>(p, s); break;
+    case FIRST | OS_LAST_AB: launch_os<FIRST | OS_LAST_AB>(p, s); break;
+    case FIRST | OS_LAST_AB | OS_FOREST: launch_os<FIRST | OS_LAST_AB | OS_FOREST>(p, s); break;
+    case OS_PAYLOAD_UV | OS_WRITE_KEYS: launch_os<OS_PAYLOAD_UV | OS_WRITE_KEYS>(p, s); break;
+    case OS_PAYLOAD_UV | OS_LAST_AB: launch_os<OS_PAYLOAD_UV | OS_LAST_AB>(p, s); break;
     case OS_WRITE_KEYS: launch_os<OS_WRITE_KEYS>(p, s); break;
-    case OS_GATHER: launch_os<OS_GATHER>(p, s); break;
-    case OS_GATHER | OS_FOREST: launch_os<OS_GATHER | OS_FOREST>(p, s); break;
-    case OS_KEY_FROM_W | OS_GEN_VALS | OS_GATHER: launch_os<OS_KEY_FROM_W | OS_GEN_VALS | OS_GATHER>(p, s); break;
-    case OS_KEY_FROM_W | OS_GEN_VALS | OS_GATHER | OS_FOREST: launch_os<OS_KEY_FROM_W | OS_GEN_VALS | OS_GATHER | OS_FOREST>(p, s); break;
     default: break;
     }
 }
