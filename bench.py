@@ -41,6 +41,12 @@ WORKLOADS = {
                      desc="skewed path, w_i = fp32(i + U(0,0.5))"),
     "rrt_1e4": dict(family="rrt", n=10**4, seed=0,
                     desc="random recursive tree, uniform fp32 weights k*2^-24"),
+    "serving": dict(family="serving", n=2000, seed=5,
+                    desc="Poisson arrivals of random recursive trees, vertex counts "
+                         "log-uniform in [1e3, 1e7], uniform fp32 weights"),
+    "batched_4096": dict(family="batch", n=4096, seed=4,
+                         desc="4096 trees, vertex counts log-uniform in [1e2, 1e6], "
+                              "random recursive or skewed path by a fair coin"),
 }
 
 
@@ -55,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="skip the path family line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--async-api", action="store_true",
+                    help="time pandora_dendrogram_async (worst-case level count, no host sync)")
     return ap.parse_args()
 
 
@@ -148,24 +156,28 @@ class ClockSampler:
 
 # ---- algorithmic bytes per kernel (the model stated in the design doc) ---------
 def sort_weight_bytes(m, launches):
-    """Bytes of the (weight, index) sort passes: first 12 B/edge (read w, write
-    key+index), middle 16, last 28 (read key+index, write perm, gather u, v,
-    write (u, v)); a single pass 24."""
+    """Bytes of the (weight, index) sort passes, which carry the endpoints:
+    first pass 28 B/edge (read w, u, v; write key, index, u, v), middle 32
+    (read and write 16), last 28 (read 16; write index 4 and (u, v) 8); a
+    single pass 24."""
     if launches == 0:
         return 0
     if launches == 1:
         return 24 * m
-    return (12 + 16 * (launches - 2) + 28) * m
+    return (28 + 32 * (launches - 2) + 28) * m
+
+
+# per element of the kernel's launch size (edges or vertices of the level)
+MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark": 25,
+               "ptr_init": 28, "compress": 16, "compact": 35, "expand": 25, "link": 16,
+               "check_offsets": 16, "fill": 4}
 
 
 def model_bytes(name, prof_entry, m, n_passes_w):
     e = prof_entry["elements"]
-    per = {"hist_weights": 4, "onesweep_chains": 16, "mark": 16, "ptr_init": 28,
-           "compress": 12, "compact": 30, "expand": 25, "link": 16, "check_offsets": 16,
-           "fill": 4}
     if name == "onesweep_weights":
         return sort_weight_bytes(m, n_passes_w) * (prof_entry["launches"] // max(n_passes_w, 1))
-    return per.get(name, 0) * e
+    return MODEL_BYTES.get(name, 0) * e
 
 
 def recorded_traffic(kernel):
@@ -259,10 +271,225 @@ def time_device(pd, torch, t, steps, warmup, profile=True):
     return dict(u=u, v=v, w=w, ws=ws, ep=ep, vp=vp)
 
 
+def run_batched(args):
+    """Batched workload: the whole batch as one forest (one async call,
+    captured in a CUDA graph) against one call per tree on the same GPU."""
+    import numpy as np
+    import torch
+    import paper_2401_06089_gb300 as pd
+    from paper_2401_06089_gb300 import inputs
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    spec = WORKLOADS[args.workload]
+    n_trees = args.n or spec["n"]
+    b = inputs.batch(n_trees, 100, 1_000_000, seed=spec["seed"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    u = torch.from_numpy(b.u).to(dev)
+    v = torch.from_numpy(b.v).to(dev)
+    w = torch.from_numpy(b.w).to(dev)
+    off = torch.from_numpy(b.edge_offsets).to(dev)
+    m = b.m
+    ws = torch.empty(pd.workspace_size(m, b.n_trees), dtype=torch.uint8, device=dev)
+    ep = torch.empty(m, dtype=torch.int32, device=dev)
+    vp = torch.empty(m + b.n_trees, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # warm-up, then capture the batched call once
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(max(args.warmup, 3)):
+            pd.dendrogram_batched_async(u, v, w, off, ws, (ep, vp))
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    pd.workspace_status(ws)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pd.dendrogram_batched_async(u, v, w, off, ws, (ep, vp))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.6)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pd.profile_start(timing=False)
+    a = torch.cuda.Event(enable_timing=True)
+    z = torch.cuda.Event(enable_timing=True)
+    sampler.start()
+    a.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    z.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    pd.workspace_status(ws)
+    prof = pd.profile_read()
+    ms = a.elapsed_time(z) / args.steps
+    if dist:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * m / (ms / 1e3)
+
+    # kernel split: blocking batched calls with per-kernel CUDA-event timing
+    pd.profile_start(timing=True)
+    for _ in range(2):
+        _, _, bstats = pd.dendrogram_batched(u, v, w, off, workspace=ws, out=(ep, vp), stats=True)
+    torch.cuda.synchronize()
+    bprof = pd.profile_read()
+    blocking_ms = sum((e["ms"] or 0.0) for e in bprof.values()) / 2
+    kern = {k: {"launches": e["launches"] // 2, "ms": e["ms"] / 2}
+            for k, e in bprof.items() if e["launches"]}
+
+    # one call per tree: blocking calls, then asynchronous calls back to back
+    views = []
+    for t in range(b.n_trees):
+        e0, e1 = int(b.edge_offsets[t]), int(b.edge_offsets[t + 1])
+        views.append((u[e0:e1], v[e0:e1], w[e0:e1], ep[e0:e1], vp[e0 + t:e1 + t + 1]))
+    for x in views[:8]:
+        pd.dendrogram(x[0], x[1], x[2], workspace=ws, out=(x[3], x[4]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for x in views:
+        pd.dendrogram(x[0], x[1], x[2], workspace=ws, out=(x[3], x[4]))
+    torch.cuda.synchronize()
+    per_tree_blocking_ms = (time.perf_counter() - t0) * 1e3
+    a.record(stream)
+    for x in views:
+        pd.dendrogram_async(x[0], x[1], x[2], ws, (x[3], x[4]))
+    z.record(stream)
+    torch.cuda.synchronize()
+    per_tree_async_ms = a.elapsed_time(z)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_trees": b.n_trees, "total_edges": m,
+                   "family": spec["desc"], "seed": spec["seed"],
+                   "mode": "one forest, pandora_dendrogram_batched_async captured in a CUDA graph",
+                   "l2": "inputs larger than L2"},
+        "per_tree_blocking_ms": per_tree_blocking_ms,
+        "per_tree_async_ms": per_tree_async_ms,
+        "speedup_vs_per_tree_blocking": per_tree_blocking_ms / ms,
+        "speedup_vs_per_tree_async": per_tree_async_ms / ms,
+        "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
+        "blocking_kernel_ms": blocking_ms,
+        "blocking_kernels": kern,
+        "levels": bstats["level_edges"],
+        "clocks": sampler.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_serving(args):
+    """Continuous batching under Poisson arrivals (p50/p99 latency, edges/s)
+    against one blocking call per request on the same trace."""
+    import numpy as np
+    import torch
+    import paper_2401_06089_gb300 as pd
+    from paper_2401_06089_gb300 import inputs
+    from paper_2401_06089_gb300.serving import DendrogramServer, Request, run_trace
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        torch.cuda.set_device(local)
+    spec = WORKLOADS["serving"]
+    rng = np.random.default_rng(spec["seed"])
+    n_pool = 40
+    sizes = inputs.log_uniform_sizes(rng, n_pool, 1000, 10_000_000)
+    pool = []
+    for k, n in enumerate(sizes):
+        t = inputs.rrt(int(n), seed=int(rng.integers(1 << 30)))
+        pool.append((torch.from_numpy(t.u).cuda(), torch.from_numpy(t.v).cuda(),
+                     torch.from_numpy(t.w).cuda()))
+    torch.cuda.synchronize()
+    mean_m = float(np.mean([p[2].numel() for p in pool]))
+    budget = 60 << 30
+
+    def trace(n_req, rate, seed):
+        r2 = np.random.default_rng(seed)
+        pick = r2.integers(0, n_pool, size=n_req)
+        arr = (np.cumsum(r2.exponential(1.0 / rate, size=n_req)) if rate else np.zeros(n_req))
+        reqs = [Request(i, *pool[int(p)]) for i, p in enumerate(pick)]
+        return reqs, arr.tolist()
+
+    def serve(reqs, arr):
+        server = DendrogramServer(budget, max_batch_edges=32_000_000, max_batch_trees=1024,
+                                  n_streams=3)
+        t0 = time.perf_counter()
+        res = run_trace(server, reqs, arr)
+        wall = time.perf_counter() - t0
+        return res, wall, server
+
+    # saturated throughput: a backlog of requests all present at t = 0
+    reqs, arr = trace(300, None, 11)
+    serve(reqs[:20], arr[:20])   # warm-up
+    res, wall, _ = serve(reqs, arr)
+    sat = sum(r.m for r in reqs) / wall
+    # one blocking call per request on the same backlog
+    for r in reqs[:5]:
+        pd.dendrogram(r.u, r.v, r.w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        pd.dendrogram(r.u, r.v, r.w)
+    torch.cuda.synchronize()
+    per_req_wall = time.perf_counter() - t0
+    per_req_rate = sum(r.m for r in reqs) / per_req_wall
+    # Poisson arrivals at 70% of the saturated rate
+    n_req = args.n or spec["n"]
+    rate = 0.7 * sat / mean_m
+    reqs, arr = trace(n_req + 200, rate, 12)
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid).replace("GPU-", "")
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.6)
+    sampler.start()
+    res, wall, server = serve(reqs, arr)
+    sampler.stop()
+    res = [r for r in res if r.rid >= 200]
+    lat = np.array([r.latency for r in res]) * 1e3
+    served_edges = sum(r.edge_parent.numel() for r in res)
+    t_first = min(r.t_arrival for r in res)
+    t_last = max(r.t_done for r in res)
+    line = {
+        "metric": METRIC, "value": served_edges / (t_last - t_first), "unit": UNIT,
+        "n_gpus": 1, "steps": n_req, "warmup": 200, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "serving", "requests": n_req, "pool_trees": n_pool,
+                   "family": spec["desc"], "mean_edges": mean_m, "arrival_rate_per_s": rate,
+                   "hbm_budget_bytes": budget, "streams": 3, "max_batch_edges": 32_000_000},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean())},
+        "saturated_edges_per_s": sat,
+        "per_request_blocking_edges_per_s": per_req_rate,
+        "speedup_saturated_vs_per_request": sat / per_req_rate,
+        "max_batches_in_flight": server.max_inflight,
+        "clocks": sampler.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload.startswith("batched"):
+        return run_batched(args)
     import numpy as np
     import torch
     import paper_2401_06089_gb300 as pd
@@ -304,13 +531,30 @@ def main():
     sampler.start()
     for k in range(args.steps):
         evs[k][0].record(stream)
-        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        if args.async_api:
+            pd.dendrogram_async(u, v, w, ws, (ep, vp))
+        else:
+            pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     sampler.stop()
     prof = pd.profile_read()
+    timing_note = "CUDA events inside the timed region"
+    if args.async_api:
+        # the asynchronous path only counts launches; time the kernels on
+        # blocking calls of the same tree right after the timed region
+        launches_async = sum(e["launches"] for e in prof.values())
+        pd.profile_start(timing=True)
+        for _ in range(args.steps):
+            pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        torch.cuda.synchronize()
+        prof = pd.profile_read()
+        for e in prof.values():
+            e["launches_async"] = None
+        timing_note = ("kernel split from blocking calls after the timed region; "
+                       f"{launches_async} launches in the timed region")
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     if dist:
@@ -359,6 +603,8 @@ def main():
         "gpu_launches": sum(e["launches"] for e in prof.values()),
         "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
         "kernels": kernels,
+        "kernel_timing": timing_note,
+        "api": "pandora_dendrogram_async" if args.async_api else "pandora_dendrogram",
         "levels": stats["level_edges"],
         "clocks": sampler.summary(),
     }

@@ -136,6 +136,30 @@ int pandora_dendrogram_batched_ws(const int32_t *u, const int32_t *v, const floa
                                   size_t workspace_bytes, pandora_stats *stats, void *stream);
 
 /*
+ * Asynchronous variants (same arguments as the *_ws entry points, minus the
+ * statistics).  They enqueue the whole pipeline on `stream` and return at
+ * once: no host synchronisation, no allocation, no host memory read by the
+ * enqueued work, so a call can be captured into a CUDA graph and replayed.
+ * The contraction loop is enqueued for its worst case, ceil(log2(m + 1))
+ * levels (Section 4.2); kernels of levels past the last one exit at once.
+ * The return value reports argument errors only; errors found by the kernels
+ * stay in the workspace's status word until pandora_workspace_status() reads
+ * it.  The workspace must not be shared by calls in flight at the same time.
+ */
+int pandora_dendrogram_async(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                             int32_t *edge_parent, int32_t *vertex_parent, void *workspace,
+                             size_t workspace_bytes, void *stream);
+int pandora_dendrogram_batched_async(const int32_t *u, const int32_t *v, const float *w,
+                                     const int64_t *edge_offsets, int64_t n_trees,
+                                     int64_t total_edges, int32_t *edge_parent,
+                                     int32_t *vertex_parent, void *workspace,
+                                     size_t workspace_bytes, void *stream);
+
+/* Waits for `stream` and returns the device status word of the last call
+ * that used `workspace` (PANDORA_OK when it found no error). */
+int pandora_workspace_status(const void *workspace, void *stream);
+
+/*
  * Allocation-free variant of pandora_dendrogram.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at the time of the call -- for example code whose device
@@ -143,7 +167,7 @@ int pandora_dendrogram_batched_ws(const int32_t *u, const int32_t *v, const floa
  * the GPU up front), or a latency-critical loop in which cudaMalloc/cudaFree
  * would synchronise the device.  It takes the same arguments and gives the
  * same result as pandora_dendrogram, but its scratch memory is a fixed
- * 20 MiB array in the library's device image (held by every GPU that loads
+ * 32 MiB array in the library's device image (held by every GPU that loads
  * the library until the process exits), so it accepts at most
  * PANDORA_NOALLOC_MAX_EDGES edges and returns PANDORA_ERR_SIZE_LIMIT above
  * that.  It calls no cudaMalloc, cudaFree or other allocating routine.

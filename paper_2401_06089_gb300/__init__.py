@@ -9,11 +9,14 @@ no CPU fallback.
 from ._binding import (  # noqa: F401
     PandoraError,
     dendrogram,
+    dendrogram_async,
     dendrogram_batched,
+    dendrogram_batched_async,
     library_path,
     profile_read,
     profile_start,
     load_library,
     status_string,
     workspace_size,
+    workspace_status,
 )

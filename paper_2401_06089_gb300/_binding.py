@@ -78,11 +78,16 @@ def load_library():
         lib.pandora_status_string.argtypes = [ctypes.c_int]
         lib.pandora_status_string.restype = ctypes.c_char_p
         lib.pandora_version.argtypes = []
+        lib.pandora_dendrogram_async.argtypes = [P, P, P, I64, P, P, P, SZ, P]
+        lib.pandora_dendrogram_batched_async.argtypes = [P, P, P, P, I64, I64, P, P, P, SZ, P]
+        lib.pandora_workspace_status.argtypes = [P, P]
         lib.pandora_profile_start.argtypes = [ctypes.c_int]
         lib.pandora_profile_read.argtypes = [P]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
-                     "pandora_version", "pandora_profile_start", "pandora_profile_read"):
+                     "pandora_version", "pandora_profile_start", "pandora_profile_read",
+                     "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
+                     "pandora_workspace_status"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -234,3 +239,65 @@ def dendrogram_batched(u, v, w, edge_offsets, *, workspace=None, stats: bool = F
     if stats:
         return ep, vp, _stats_dict(st_out)
     return ep, vp
+
+
+def dendrogram_async(u, v, w, workspace, out):
+    """Enqueue ``pandora_dendrogram_async`` on the current stream and return.
+
+    Nothing is synchronised or allocated, so the call can be captured in a
+    CUDA graph.  ``out`` = (edge_parent, vertex_parent) receives the result
+    once the stream reaches it; device-detected errors are read with
+    ``workspace_status(workspace)``.
+    """
+    torch = _torch()
+    lib = load_library()
+    _check(w, torch.float32, "w")
+    dev = w.device
+    m = w.numel()
+    _check(u, torch.int32, "u", dev, m)
+    _check(v, torch.int32, "v", dev, m)
+    ep, vp = out
+    _check(ep, torch.int32, "edge_parent", dev, m)
+    _check(vp, torch.int32, "vertex_parent", dev, m + 1)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_dendrogram_async(_ptr(u), _ptr(v), _ptr(w), m, _ptr(ep), _ptr(vp),
+                                          _ptr(workspace), workspace.numel(), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram_async")
+
+
+def dendrogram_batched_async(u, v, w, edge_offsets, workspace, out):
+    """Enqueue ``pandora_dendrogram_batched_async`` (see ``dendrogram_async``)."""
+    torch = _torch()
+    lib = load_library()
+    _check(w, torch.float32, "w")
+    dev = w.device
+    m = w.numel()
+    _check(u, torch.int32, "u", dev, m)
+    _check(v, torch.int32, "v", dev, m)
+    _check(edge_offsets, torch.int64, "edge_offsets", dev)
+    n_trees = edge_offsets.numel() - 1
+    ep, vp = out
+    _check(ep, torch.int32, "edge_parent", dev, m)
+    _check(vp, torch.int32, "vertex_parent", dev, m + n_trees)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_dendrogram_batched_async(_ptr(u), _ptr(v), _ptr(w), _ptr(edge_offsets),
+                                                  n_trees, m, _ptr(ep), _ptr(vp),
+                                                  _ptr(workspace), workspace.numel(), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram_batched_async")
+
+
+def workspace_status(workspace, raise_on_error: bool = True) -> int:
+    """Wait for the current stream and return the workspace's device status."""
+    torch = _torch()
+    lib = load_library()
+    dev = workspace.device
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_workspace_status(_ptr(workspace), stream)
+    if st and raise_on_error:
+        raise PandoraError(st, "device status")
+    return st

@@ -23,14 +23,25 @@ constexpr u32 SPIN_LIMIT = 1u << 22;       // bound of every device-side wait lo
 
 // ---- control block kept at the start of the workspace ----------------------
 struct Ctrl {
-    int status;               // first device-detected error (pandora_status)
-    int pad0;
-    u64 count_roots;          // supervertices of the next level
-    u64 count_alpha;          // alpha-edges = edges of the next level
-    u32 tile_counter[16];     // dynamic tile ids of single-pass kernels
-    u32 hist1[4][256];        // digit histograms of the (weight, index) sort
-    u32 hist2[4][256];        // digit histograms of the chain-key sort
+    int status;                    // first device-detected error (pandora_status)
+    int n_levels;                  // contraction levels run; set by the level that
+                                   // has no alpha-edge (0 while the loop runs)
+    u64 lvl_m[MAX_LEVELS + 1];     // edges of level l (device truth)
+    u64 lvl_n[MAX_LEVELS + 1];     // vertices of level l
+    u64 n_deep;                    // vertices left to union-find by the bounded walk
+    u32 tile_counter[16];          // dynamic tile ids of single-pass kernels
+    u32 hist1[4][256];             // digit histograms of the (weight, index) sort
+    u32 hist2[4][256];             // digit histograms of the chain-key sort
 };
+
+// Element count produced on the device, clamped to the buffer capacity the
+// host sized the launch for (a larger count only arises from invalid input,
+// which the producing kernel reports).
+__device__ __forceinline__ i64 dev_count(const u64 *d, i64 cap)
+{
+    const u64 c = *(const volatile u64 *)d;
+    return c > (u64)cap ? cap : (i64)c;
+}
 
 __device__ __forceinline__ void set_status(int *status, int code)
 {
@@ -113,6 +124,67 @@ __device__ __forceinline__ u64 lookback_exclusive(u64 *lb, u32 tile, u64 aggrega
     }
     st_relaxed(lb + tile, LB_INC | (excl + aggregate));
     return excl;
+}
+
+// ---- TMA bulk copies (cp.async.bulk) completed on an mbarrier ---------------
+__device__ __forceinline__ u32 smem_u32(const void *p)
+{
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64 *bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned); completion is counted on `bar`
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, u32 bytes, u64 *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`.  On timeout the status word
+// records PANDORA_ERR_ITERATION_LIMIT and the wait goes on, bounded again,
+// so that the block never leaves while its own copies are still landing in
+// its shared memory; returns false if both bounds ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity, int *status)
+{
+    for (u32 i = 0; i < SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    set_status(status, PANDORA_ERR_ITERATION_LIMIT);
+    for (u32 i = 0; i < SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
 }
 
 // Tree id of a global edge index in forest mode (binary search of the

@@ -23,8 +23,19 @@ namespace {
 __global__ void __launch_bounds__(256) expand_kernel(const ExpandParams p, const LevelTable t)
 {
     __shared__ u32 s_h[4 * RADIX];
+    __shared__ i64 s_nv[MAX_LEVELS];   // vertices of every level, clamped to capacity
     for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x)
         s_h[i] = 0;
+    for (int l = threadIdx.x; l < MAX_LEVELS; l += blockDim.x)
+        s_nv[l] = l < p.max_levels ? dev_count(p.lvl_n + l, t.n_cap[l]) : 0;
+    // levels actually run; 0 means the loop never met a level without
+    // alpha-edges within the launched bound (only on invalid input)
+    int n_levels = *p.d_n_levels;
+    if (n_levels == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+        n_levels = p.max_levels;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const i64 stride = (i64)gridDim.x * blockDim.x;
@@ -36,10 +47,18 @@ __global__ void __launch_bounds__(256) expand_kernel(const ExpandParams p, const
             const int l0 = p.lev[r];
             i32 sv = p.start[r];
             key = NONE;
-            for (int l = l0 + 1; l < p.n_levels; ++l) {
+            for (int l = l0 + 1; l < n_levels; ++l) {
+                if (sv < 0 || (i64)sv >= s_nv[l]) {   // only after an earlier error
+                    set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+                    break;
+                }
                 const int2 rec = __ldg(t.rec[l] + sv);
-                const u32 c = (u32)rec.x;
+                u32 c = (u32)rec.x;
                 if ((u32)r < (c >> 1)) {   // an isolated supervertex (c = NONE) ends here too
+                    if (c != NONE && (i64)(c >> 1) >= p.m) {   // only after an earlier error
+                        set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+                        c = NONE;
+                    }
                     key = c;
                     break;
                 }
@@ -109,6 +128,12 @@ __global__ void check_offsets_kernel(const i64 *off, i64 n_trees, i64 total, int
         set_status(status, PANDORA_ERR_INVALID_ARGUMENT);
 }
 
+__global__ void set_u64_pair_kernel(u64 *a, u64 va, u64 *b, u64 vb)
+{
+    *a = va;
+    *b = vb;
+}
+
 __global__ void fill_kernel(i32 *p, i64 n, i32 value)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,6 +168,11 @@ void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, c
 {
     check_offsets_kernel<<<(unsigned)((n_trees + 1 + 255) / 256), 256, 0, s>>>(off, n_trees, total,
                                                                               status);
+}
+
+void launch_set_u64_pair(u64 *a, u64 va, u64 *b, u64 vb, cudaStream_t s)
+{
+    set_u64_pair_kernel<<<1, 1, 0, s>>>(a, va, b, vb);
 }
 
 void launch_fill(i32 *p, i64 n, i32 value, cudaStream_t s)

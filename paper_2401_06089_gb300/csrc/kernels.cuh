@@ -84,13 +84,24 @@ constexpr u64 NO_EDGE = ~0ull;
 
 struct LevelParams {
     int level;
-    i64 m;                 // edges of this level
-    i64 n;                 // vertices of this level
+    // sizes: the device counts are the truth; *_cap bound them (buffer
+    // capacity) and *_grid is what the host sized the launch for
+    const u64 *d_m;        // edges of this level
+    const u64 *d_n;        // vertices of this level
+    u64 *d_m_next;         // alpha-edges = edges of the next level
+    u64 *d_n_next;         // roots = vertices of the next level
+    i64 m_cap, n_cap;
+    i64 m_grid, n_grid;
+    int *d_n_levels;       // Ctrl::n_levels
     const int2 *ab;        // endpoints (level vertex ids), ascending rank
     const u32 *er;         // global rank of each edge (nullptr on level 0: rank = index)
     u64 *min_word;         // [n] lightest-incident-edge word (see above)
     unsigned char *maybe;  // [m] bit s: the edge may be the lightest at endpoint s
     i32 *ptr;              // [n] pointer forest scratch
+    i32 *deep;             // [n] vertices the bounded walk left unresolved (list)
+    i32 *uf;               // [n] union-find parents of those vertices
+    i32 *root_of;          // [n] dense root id, stored at union-find representatives
+    u64 *d_n_deep;         // length of the deep list
     i32 *vmap;             // [n] vertex -> supervertex (level 0)
     int2 *rec;             // [n] {chain key, supervertex} kept for the expansion (levels >= 1)
     // level 0 only: vertex_parent output
@@ -104,16 +115,15 @@ struct LevelParams {
     i64 cap_next;          // capacity of ab_next / er_next
     unsigned char *lev;    // [M] contraction level of each edge (by rank)
     i32 *start;            // [M] supervertex holding the edge on the next level
-    u64 *lb;               // look-back words (zeroed per kernel)
-    u32 *tile_counter;     // two counters (zeroed)
-    u64 *count_roots;
-    u64 *count_alpha;
+    u64 *lb;               // look-back words (zeroed per level)
+    u32 *tile_counter;     // two counters (zeroed per level)
     int *status;
 };
 
+void launch_init_level(const LevelParams &p, cudaStream_t s);   // min_word = NO_EDGE
 void launch_mark(const LevelParams &p, cudaStream_t s);
 void launch_ptr_init(const LevelParams &p, cudaStream_t s);
-void launch_compress(const LevelParams &p, cudaStream_t s);
+void launch_compress(const LevelParams &p, cudaStream_t s);   // walk + union-find fallback
 void launch_compact(const LevelParams &p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -121,11 +131,14 @@ void launch_compact(const LevelParams &p, cudaStream_t s);
 // ---------------------------------------------------------------------------
 struct LevelTable {
     const int2 *rec[MAX_LEVELS];   // {chain key, supervertex} of every vertex of level l >= 1
+    i64 n_cap[MAX_LEVELS];         // capacity of rec[l]
 };
 
 struct ExpandParams {
     i64 m;
-    int n_levels;
+    int max_levels;        // levels launched (bound); the device count is in *d_n_levels
+    const int *d_n_levels;
+    const u64 *lvl_n;      // Ctrl::lvl_n (vertices of every level)
     const unsigned char *lev;
     const i32 *start;
     const u32 *perm;
@@ -154,6 +167,8 @@ void launch_link(const LinkParams &p, cudaStream_t s);
 
 // forest mode: check the offsets (off[0] == 0, non-decreasing, off[T] == M)
 void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, cudaStream_t s);
+// two 64-bit device words set from kernel parameters (graph-capture safe)
+void launch_set_u64_pair(u64 *a, u64 va, u64 *b, u64 vb, cudaStream_t s);
 // vertex_parent = -1 for every vertex of an edgeless input
 void launch_fill(i32 *p, i64 n, i32 value, cudaStream_t s);
 

@@ -81,196 +81,389 @@ __device__ __forceinline__ void tile_rank(const bool (&flag)[LV_ITEMS], u32 (&ra
     *tile_total = s_total;
 }
 
+// Level kernels run only while the loop is open: once a level without
+// alpha-edges has set n_levels, kernels launched for later (bound) levels
+// exit at once.
+__device__ __forceinline__ bool loop_closed(const LevelParams &p)
+{
+    return *(const volatile int *)p.d_n_levels != 0;
+}
+
+__global__ void __launch_bounds__(256) init_level_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    const i64 n = dev_count(p.d_n, p.n_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *p.d_n_deep = 0;
+    for (i64 x = (i64)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (i64)gridDim.x * blockDim.x)
+        p.min_word[x] = NO_EDGE;
+}
+
 template <bool LEVEL0>
 __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
 {
-    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.m)
+    if (loop_closed(p))
         return;
-    const int2 e = p.ab[i];
-    const u64 r = LEVEL0 ? (u64)i : (u64)p.er[i];
-    const u64 wa = (r << 32) | ((u64)(u32)e.y << 1);        // at e.x: other end e.y, side 0
-    const u64 wb = (r << 32) | ((u64)(u32)e.x << 1) | 1u;   // at e.y: other end e.x, side 1
-    // A plain read first keeps hub vertices (stars) from serialising on one
-    // address: the word only decreases, so a stale read may cost an unneeded
-    // atomic but never a wrong skip.  The value seen (old) decides whether
-    // this edge can still be the lightest at that endpoint.
-    u64 old = p.min_word[e.x];
-    if (old > wa)
-        old = atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
-    const bool maybe_a = old > wa;
-    old = p.min_word[e.y];
-    if (old > wb)
-        old = atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
-    const bool maybe_b = old > wb;
-    p.maybe[i] = (unsigned char)((maybe_a ? 1 : 0) | (maybe_b ? 2 : 0));
+    const i64 m = dev_count(p.d_m, p.m_cap);
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (i64)gridDim.x * blockDim.x) {
+        const int2 e = p.ab[i];
+        const u64 r = LEVEL0 ? (u64)i : (u64)p.er[i];
+        const u64 wa = (r << 32) | ((u64)(u32)e.y << 1);        // at e.x: other end e.y, side 0
+        const u64 wb = (r << 32) | ((u64)(u32)e.x << 1) | 1u;   // at e.y: other end e.x, side 1
+        // A plain read first keeps hub vertices (stars) from serialising on one
+        // address: the word only decreases, so a stale read may cost an unneeded
+        // atomic but never a wrong skip.  The value seen (old) decides whether
+        // this edge can still be the lightest at that endpoint.
+        u64 old = p.min_word[e.x];
+        if (old > wa)
+            old = atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
+        const bool maybe_a = old > wa;
+        old = p.min_word[e.y];
+        if (old > wb)
+            old = atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
+        const bool maybe_b = old > wb;
+        p.maybe[i] = (unsigned char)((maybe_a ? 1 : 0) | (maybe_b ? 2 : 0));
+    }
+}
+
+// Claims the next tile of a dynamically scheduled kernel (tile ids are handed
+// out in launch order, which keeps the look-back deadlock-free).
+__device__ __forceinline__ u32 claim_tile(u32 *counter, u32 *s_tile)
+{
+    __syncthreads();   // everyone has read the previous tile id
+    if (threadIdx.x == 0)
+        *s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    return *s_tile;
 }
 
 template <bool LEVEL0, bool FOREST>
 __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams p)
 {
+    if (loop_closed(p))
+        return;
+    const i64 n = dev_count(p.d_n, p.n_cap);
+    const i64 tiles = level_tiles(n);
     __shared__ u32 s_tile;
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(p.tile_counter, 1u);
-    __syncthreads();
-    const u32 tile = s_tile;
-    const i64 tile_base = (i64)tile * LV_TILE;
-    bool root[LV_ITEMS];
-    i32 nxt[LV_ITEMS];
+    // persistent: a block keeps claiming tiles until the level is covered, so
+    // a grid sized for the worst case costs one atomic per block, not per tile
+    for (u32 tile = claim_tile(p.tile_counter, &s_tile); (i64)tile < tiles;
+         tile = claim_tile(p.tile_counter, &s_tile)) {
+        const i64 tile_base = (i64)tile * LV_TILE;
+        bool root[LV_ITEMS];
+        i32 nxt[LV_ITEMS];
 #pragma unroll
-    for (int it = 0; it < LV_ITEMS; ++it) {
-        const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
-        root[it] = false;
-        nxt[it] = (i32)x;
-        if (x >= p.n)
-            continue;
-        const u64 wx = p.min_word[x];
-        if (wx == NO_EDGE) {
-            root[it] = true;   // isolated vertex: a finished tree of a forest
-        } else {
-            const u32 r = (u32)(wx >> 32);
-            const i32 y = (i32)((wx >> 1) & 0x7FFFFFFFu);
-            if (y == (i32)x) {
-                root[it] = true;   // self-loop: reported by compact on the level above
+        for (int it = 0; it < LV_ITEMS; ++it) {
+            const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
+            root[it] = false;
+            nxt[it] = (i32)x;
+            if (x >= n)
+                continue;
+            const u64 wx = p.min_word[x];
+            if (wx == NO_EDGE) {
+                root[it] = true;   // isolated vertex: a finished tree of a forest
             } else {
-                // a leaf edge (lightest at both ends) closes a 2-cycle; its
-                // smaller endpoint becomes the root of the component
-                const u64 wy = p.min_word[y];
-                root[it] = ((u32)(wy >> 32) == r) && ((i32)x < y);
-                nxt[it] = y;
+                const u32 r = (u32)(wx >> 32);
+                const i32 y = (i32)((wx >> 1) & 0x7FFFFFFFu);
+                if (y == (i32)x || (i64)y >= n) {
+                    root[it] = true;   // self-loop (reported by compact on the level above)
+                } else {
+                    // a leaf edge (lightest at both ends) closes a 2-cycle; its
+                    // smaller endpoint becomes the root of the component
+                    const u64 wy = p.min_word[y];
+                    root[it] = ((u32)(wy >> 32) == r) && ((i32)x < y);
+                    nxt[it] = y;
+                }
+                if (LEVEL0) {
+                    i32 par = (i32)__ldg(p.perm + r);   // Eq. 1, caller edge id
+                    if (FOREST)
+                        par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, par));
+                    p.vertex_parent[x] = par;
+                }
             }
-            if (LEVEL0) {
-                i32 par = (i32)__ldg(p.perm + r);   // Eq. 1, caller edge id
-                if (FOREST)
-                    par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, par));
-                p.vertex_parent[x] = par;
-            }
+            if (LEVEL0 && wx == NO_EDGE)
+                p.vertex_parent[x] = -1;
         }
-        if (LEVEL0 && wx == NO_EDGE)
-            p.vertex_parent[x] = -1;
-    }
-    u32 rank[LV_ITEMS];
-    u64 base;
-    u32 total;
-    tile_rank(root, rank, tile, p.lb, p.status, &base, &total);
+        u32 rank[LV_ITEMS];
+        u64 base;
+        u32 total;
+        tile_rank(root, rank, tile, p.lb, p.status, &base, &total);
 #pragma unroll
-    for (int it = 0; it < LV_ITEMS; ++it) {
-        const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
-        if (x < p.n)
-            p.ptr[x] = root[it] ? ~(i32)rank[it] : nxt[it];
+        for (int it = 0; it < LV_ITEMS; ++it) {
+            const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
+            if (x < n)
+                p.ptr[x] = root[it] ? ~(i32)rank[it] : nxt[it];
+        }
+        if (threadIdx.x == 0 && (i64)tile == tiles - 1)
+            *p.d_n_next = base + total;
     }
-    if (threadIdx.x == 0 && tile == (u32)(level_tiles(p.n) - 1))
-        *p.count_roots = base + total;
 }
 
-// Root finding with path halving.  Writes the supervertex of x; on levels
-// >= 1 also the chain key 2*rank(P(x)) + side that the expansion compares
-// against, packed with it.
+// Root finding, in two parts.
+//
+// 1. compress_walk: every vertex follows its pointers, read-only, for at most
+//    WALK_STEPS steps.  Lightest-edge pointer forests of trees with unordered
+//    weights are shallow (depth <= 7 on random recursive, caterpillar and
+//    binary trees with random weights), so almost every vertex reaches a root
+//    or a vertex already resolved (tagged ~dense id), records its supervertex
+//    and tags itself.  A vertex still unresolved after WALK_STEPS steps is
+//    appended to the deep list.
+// 2. Only when the deep list is not empty (long monotone chains, e.g. a path
+//    whose weights increase along it), union-find over the deep vertices:
+//    uf_union hooks the larger representative under the smaller one (CAS,
+//    path halving) for every deep vertex and its deep pointer target; the top
+//    of each deep component (its pointer target is resolved) stores the dense
+//    root id at the component's representative (uf_tops), and uf_finish hands
+//    it to every member.  This is the union-find contraction the paper uses
+//    (after Jaiganesh and Burtscher), applied where pointer chasing would cost
+//    log(depth) rounds per vertex.
+constexpr int WALK_STEPS = 8;
+
 template <bool LEVEL0>
-__global__ void __launch_bounds__(256) compress_kernel(const LevelParams p)
+__device__ __forceinline__ void write_supervertex(const LevelParams &p, i64 x, i32 dense)
 {
-    const i64 x = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.n)
-        return;
-    i32 *ptr = p.ptr;
-    i32 cur = (i32)x;
-    i32 res;
-    i64 iter = 0;
-    for (;;) {
-        const i32 pc = ld_volatile(ptr + cur);
-        if (pc < 0) {
-            res = pc;
-            break;
-        }
-        const i32 g = ld_volatile(ptr + pc);
-        if (g < 0) {
-            res = g;
-            break;
-        }
-        st_volatile(ptr + cur, g);   // path halving: g is an ancestor of cur
-        cur = g;
-        if (++iter > p.n + 64) {
-            set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
-            res = ~0;
-            break;
-        }
-    }
     if (LEVEL0) {
-        p.vmap[x] = ~res;
+        p.vmap[x] = dense;
     } else {
         const u64 wx = p.min_word[x];
         const u32 ck = wx == NO_EDGE ? NONE : 2u * (u32)(wx >> 32) + (u32)(wx & 1u);
-        p.rec[x] = make_int2((i32)ck, ~res);
+        p.rec[x] = make_int2((i32)ck, dense);
     }
-    if (cur != (i32)x)
-        st_volatile(ptr + x, res);     // later walks through x stop here
+}
+
+template <bool LEVEL0>
+__global__ void __launch_bounds__(256) compress_walk_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    const i64 n = dev_count(p.d_n, p.n_cap);
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 n_round = (n + 31) & ~(i64)31;
+    for (i64 x = (i64)blockIdx.x * blockDim.x + threadIdx.x; x - lane < n_round; x += stride) {
+        bool deep = false;
+        if (x < n) {
+            i32 cur = (i32)x;
+            i32 res = 0;
+            bool done = false;
+            for (int step = 0; step < WALK_STEPS; ++step) {
+                const i32 pc = ld_volatile(p.ptr + cur);
+                if (pc < 0) {
+                    res = pc;
+                    done = true;
+                    break;
+                }
+                cur = pc;
+            }
+            if (done) {
+                write_supervertex<LEVEL0>(p, x, ~res);
+                if (cur != (i32)x)
+                    st_volatile(p.ptr + x, res);   // resolved: later walks stop here
+            } else {
+                deep = true;
+                p.uf[x] = (i32)x;
+            }
+        }
+        // warp-aggregated append to the deep list
+        const u32 ball = __ballot_sync(0xFFFFFFFFu, deep);
+        if (ball) {
+            u64 base = 0;
+            if (lane == __ffs(ball) - 1)
+                base = atomicAdd((unsigned long long *)p.d_n_deep, (unsigned long long)__popc(ball));
+            base = __shfl_sync(0xFFFFFFFFu, base, __ffs(ball) - 1);
+            if (deep)
+                p.deep[base + __popc(ball & lanemask_lt())] = (i32)x;
+        }
+    }
+}
+
+__device__ __forceinline__ i32 uf_find(i32 *uf, i32 a, int *status, i64 bound)
+{
+    i64 iter = 0;
+    for (;;) {
+        const i32 pa = ld_volatile(uf + a);
+        if (pa == a)
+            return a;
+        const i32 ga = ld_volatile(uf + pa);
+        if (ga != pa)
+            st_volatile(uf + a, ga);   // path halving (benign race: ga is an ancestor)
+        a = ga;
+        if (++iter > bound) {
+            set_status(status, PANDORA_ERR_ITERATION_LIMIT);
+            return a;
+        }
+    }
+}
+
+__device__ __forceinline__ i64 deep_count(const LevelParams &p)
+{
+    return dev_count(p.d_n_deep, p.n_cap);
+}
+
+__global__ void __launch_bounds__(256) uf_union_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    const i64 nd = deep_count(p);
+    const i64 bound = dev_count(p.d_n, p.n_cap) + 64;
+    for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nd;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 x = p.deep[k];
+        const i32 y = ld_volatile(p.ptr + x);
+        if (ld_volatile(p.ptr + y) < 0)
+            continue;   // y is resolved: x tops its deep component
+        // both deep: hook the larger representative under the smaller
+        i32 a = x, b = y;
+        for (i64 iter = 0;; ++iter) {
+            a = uf_find(p.uf, a, p.status, bound);
+            b = uf_find(p.uf, b, p.status, bound);
+            if (a == b)
+                break;
+            if (a < b) {
+                const i32 t = a;
+                a = b;
+                b = t;
+            }
+            const i32 old = atomicCAS(p.uf + a, a, b);
+            if (old == a)
+                break;
+            a = old;
+            if (iter > bound) {
+                set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
+                break;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) uf_tops_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    const i64 nd = deep_count(p);
+    const i64 bound = dev_count(p.d_n, p.n_cap) + 64;
+    for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nd;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 x = p.deep[k];
+        const i32 y = ld_volatile(p.ptr + x);
+        const i32 py = ld_volatile(p.ptr + y);
+        if (py < 0)
+            p.root_of[uf_find(p.uf, x, p.status, bound)] = ~py;
+    }
+}
+
+template <bool LEVEL0>
+__global__ void __launch_bounds__(256) uf_finish_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    const i64 nd = deep_count(p);
+    const i64 bound = dev_count(p.d_n, p.n_cap) + 64;
+    for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nd;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 x = p.deep[k];
+        write_supervertex<LEVEL0>(p, x, p.root_of[uf_find(p.uf, x, p.status, bound)]);
+    }
 }
 
 template <bool LEVEL0>
 __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p)
 {
+    if (loop_closed(p))
+        return;
+    const i64 m = dev_count(p.d_m, p.m_cap);
+    const i64 tiles = level_tiles(m);
     __shared__ u32 s_tile;
-    if (threadIdx.x == 0)
-        s_tile = atomicAdd(p.tile_counter + 1, 1u);
-    __syncthreads();
-    const u32 tile = s_tile;
-    const i64 tile_base = (i64)tile * LV_TILE;
-    bool alpha[LV_ITEMS];
-    int2 nab[LV_ITEMS];
-    u32 rr[LV_ITEMS];
+    for (u32 tile = claim_tile(p.tile_counter + 1, &s_tile); (i64)tile < tiles;
+         tile = claim_tile(p.tile_counter + 1, &s_tile)) {
+        const i64 tile_base = (i64)tile * LV_TILE;
+        bool alpha[LV_ITEMS];
+        int2 nab[LV_ITEMS];
+        u32 rr[LV_ITEMS];
 #pragma unroll
-    for (int it = 0; it < LV_ITEMS; ++it) {
-        const i64 i = tile_base + it * LV_THREADS + threadIdx.x;
-        alpha[it] = false;
-        if (i >= p.m)
-            continue;
-        const int2 e = p.ab[i];
-        const u32 r = LEVEL0 ? (u32)i : p.er[i];
-        const unsigned mb = p.maybe[i];
-        rr[it] = r;
-        // Eq. 2: an alpha-edge is the lightest incident edge of neither endpoint
-        const bool a_min = (mb & 1) && (u32)(p.min_word[e.x] >> 32) == r;
-        const bool b_min = (mb & 2) && (u32)(p.min_word[e.y] >> 32) == r;
-        const i32 va = LEVEL0 ? p.vmap[e.x] : p.rec[e.x].y;
-        if (!a_min && !b_min) {
-            const i32 vb = LEVEL0 ? p.vmap[e.y] : p.rec[e.y].y;
-            if (va == vb)
-                set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // a cycle closed up
-            alpha[it] = true;
-            nab[it] = make_int2(va, vb);
-        } else {
-            p.lev[r] = (unsigned char)p.level;
-            p.start[r] = va;
-        }
-    }
-    u32 rank[LV_ITEMS];
-    u64 base;
-    u32 total;
-    tile_rank(alpha, rank, tile, p.lb + level_tiles(p.n) + 1, p.status, &base, &total);
-#pragma unroll
-    for (int it = 0; it < LV_ITEMS; ++it) {
-        if (alpha[it]) {
-            // a tree has at most (m - 1) / 2 alpha-edges (Section 4.2); more
-            // means the input had a cycle (multi-edges): report, never overflow
-            if ((i64)rank[it] < p.cap_next) {
-                p.ab_next[rank[it]] = nab[it];
-                p.er_next[rank[it]] = rr[it];
+        for (int it = 0; it < LV_ITEMS; ++it) {
+            const i64 i = tile_base + it * LV_THREADS + threadIdx.x;
+            alpha[it] = false;
+            if (i >= m)
+                continue;
+            const int2 e = p.ab[i];
+            const u32 r = LEVEL0 ? (u32)i : p.er[i];
+            const unsigned mb = p.maybe[i];
+            rr[it] = r;
+            // Eq. 2: an alpha-edge is the lightest incident edge of neither endpoint
+            const bool a_min = (mb & 1) && (u32)(p.min_word[e.x] >> 32) == r;
+            const bool b_min = (mb & 2) && (u32)(p.min_word[e.y] >> 32) == r;
+            const i32 va = LEVEL0 ? p.vmap[e.x] : p.rec[e.x].y;
+            if (!a_min && !b_min) {
+                const i32 vb = LEVEL0 ? p.vmap[e.y] : p.rec[e.y].y;
+                if (va == vb)
+                    set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // a cycle closed up
+                alpha[it] = true;
+                nab[it] = make_int2(va, vb);
             } else {
-                set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+                p.lev[r] = (unsigned char)p.level;
+                p.start[r] = va;
             }
         }
+        u32 rank[LV_ITEMS];
+        u64 base;
+        u32 total;
+        tile_rank(alpha, rank, tile, p.lb + level_tiles(p.n_grid) + 1, p.status, &base, &total);
+#pragma unroll
+        for (int it = 0; it < LV_ITEMS; ++it) {
+            if (alpha[it]) {
+                // a tree has at most (m - 1) / 2 alpha-edges (Section 4.2); more
+                // means the input had a cycle (multi-edges): report, never overflow
+                if ((i64)rank[it] < p.cap_next) {
+                    p.ab_next[rank[it]] = nab[it];
+                    p.er_next[rank[it]] = rr[it];
+                } else {
+                    set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+                }
+            }
+        }
+        if (threadIdx.x == 0 && (i64)tile == tiles - 1) {
+            const u64 n_alpha = base + total;
+            *p.d_m_next = n_alpha;
+            // every level of a forest of T trees has n = m + T (n_next is the
+            // root count ptr_init wrote for this level)
+            if (*(volatile u64 *)p.d_n_next != n_alpha + (u64)p.n_trees)
+                set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+            if (n_alpha == 0)
+                *p.d_n_levels = p.level + 1;
+        }
     }
-    if (threadIdx.x == 0 && tile == (u32)(level_tiles(p.m) - 1))
-        *p.count_alpha = base + total;
 }
 
 }  // namespace
 
+// Blocks for n elements at per_block each, capped at a few waves of the 152
+// SMs: every level kernel loops (grid-stride or over claimed tiles), so a
+// grid sized for a worst-case bound does not launch idle blocks by the
+// million.
+static unsigned grid_for(i64 n, int per_block)
+{
+    i64 b = (n + per_block - 1) / per_block;
+    const i64 cap = 152 * 16;
+    if (b > cap)
+        b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+void launch_init_level(const LevelParams &p, cudaStream_t s)
+{
+    i64 b = (p.n_grid + 255) / 256;
+    if (b > 152 * 16)
+        b = 152 * 16;
+    init_level_kernel<<<(unsigned)(b < 1 ? 1 : b), 256, 0, s>>>(p);
+}
+
 void launch_mark(const LevelParams &p, cudaStream_t s)
 {
-    if (p.m <= 0)
-        return;
-    const unsigned blocks = (unsigned)((p.m + 255) / 256);
+    const unsigned blocks = grid_for(p.m_grid, 256);
     if (p.level == 0)
         mark_kernel<true><<<blocks, 256, 0, s>>>(p);
     else
@@ -279,7 +472,7 @@ void launch_mark(const LevelParams &p, cudaStream_t s)
 
 void launch_ptr_init(const LevelParams &p, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)level_tiles(p.n);
+    const unsigned blocks = grid_for(p.n_grid, LV_TILE);
     if (p.level == 0) {
         if (p.edge_off)
             ptr_init_kernel<true, true><<<blocks, LV_THREADS, 0, s>>>(p);
@@ -292,18 +485,23 @@ void launch_ptr_init(const LevelParams &p, cudaStream_t s)
 
 void launch_compress(const LevelParams &p, cudaStream_t s)
 {
-    const unsigned blocks = (unsigned)((p.n + 255) / 256);
+    const unsigned blocks = grid_for(p.n_grid, 256);
     if (p.level == 0)
-        compress_kernel<true><<<blocks, 256, 0, s>>>(p);
+        compress_walk_kernel<true><<<blocks, 256, 0, s>>>(p);
     else
-        compress_kernel<false><<<blocks, 256, 0, s>>>(p);
+        compress_walk_kernel<false><<<blocks, 256, 0, s>>>(p);
+    // the union-find part exits at once when the deep list is empty
+    uf_union_kernel<<<blocks, 256, 0, s>>>(p);
+    uf_tops_kernel<<<blocks, 256, 0, s>>>(p);
+    if (p.level == 0)
+        uf_finish_kernel<true><<<blocks, 256, 0, s>>>(p);
+    else
+        uf_finish_kernel<false><<<blocks, 256, 0, s>>>(p);
 }
 
 void launch_compact(const LevelParams &p, cudaStream_t s)
 {
-    if (p.m <= 0)
-        return;
-    const unsigned blocks = (unsigned)level_tiles(p.m);
+    const unsigned blocks = grid_for(p.m_grid, LV_TILE);
     if (p.level == 0)
         compact_kernel<true><<<blocks, LV_THREADS, 0, s>>>(p);
     else

@@ -4,7 +4,7 @@
 // GPU memory belongs to another allocator, or cudaMalloc/cudaFree would
 // stall a latency-critical loop), the whole dendrogram pipeline runs on a
 // fixed scratch array that is part of the library's device image.  The
-// array is 20 MiB on every GPU that loads the library, which bounds the
+// array is 32 MiB on every GPU that loads the library, which bounds the
 // input at PANDORA_NOALLOC_MAX_EDGES edges.
 #include <mutex>
 
@@ -18,7 +18,7 @@ size_t workspace_bytes(i64 M, i64 T);
 
 namespace {
 
-constexpr size_t kScratchBytes = size_t(20) << 20;
+constexpr size_t kScratchBytes = size_t(32) << 20;
 constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; host code must not use this name as an

@@ -8,6 +8,7 @@
 // Between levels the host reads back two counters (the next level's edges and
 // vertices) to size the next launches; nothing else leaves the device.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -22,11 +23,11 @@ namespace {
 // ---- optional instrumentation (pandora_profile_*) -------------------------
 enum Slot : int {
     K_HIST_WEIGHTS, K_SORT_WEIGHTS, K_MARK, K_PTR_INIT, K_COMPRESS, K_COMPACT, K_EXPAND,
-    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_SLOTS
+    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_INIT_LEVEL, K_SLOTS
 };
 const char *const kSlotNames[K_SLOTS] = {
     "hist_weights", "onesweep_weights", "mark", "ptr_init", "compress", "compact", "expand",
-    "onesweep_chains", "link", "check_offsets", "fill"};
+    "onesweep_chains", "link", "check_offsets", "fill", "init_level"};
 
 struct Profiler {
     std::mutex mu;
@@ -47,11 +48,13 @@ Profiler &profiler()
 // process-wide totals once the call's work is complete.
 class CallTimer {
   public:
-    explicit CallTimer(cudaStream_t s) : s_(s)
+    // Timing needs a host synchronisation at the end of the call, so it is
+    // only done for blocking calls; asynchronous calls only count launches.
+    CallTimer(cudaStream_t s, bool blocking) : s_(s)
     {
         Profiler &p = profiler();
         std::lock_guard<std::mutex> lock(p.mu);
-        timing_ = p.timing;
+        timing_ = p.timing && blocking;
     }
     ~CallTimer() { flush(); }
 
@@ -125,6 +128,7 @@ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, maybe, ptr, vmap0;
+    size_t deep, uf, root_of;
     size_t kept_rec, abX, erX, abY, erY, lev, start, total;
     i64 kept_cap, half_cap, lb_words;
 };
@@ -154,6 +158,9 @@ Layout make_layout(i64 M, i64 T)
     L.maybe = take(M);
     L.ptr = take(N * 4);
     L.vmap0 = take(N * 4);
+    L.deep = take(N * 4);
+    L.uf = take(N * 4);
+    L.root_of = take(N * 4);
     // vertices of all levels >= 1: n_l = m_l + T and sum_{l>=1} m_l <= M
     L.kept_cap = M + (i64)MAX_LEVELS * T + 64;
     L.kept_rec = take(L.kept_cap * 8);
@@ -175,12 +182,15 @@ Layout make_layout(i64 M, i64 T)
             return PANDORA_ERR_CUDA;       \
     } while (0)
 
+// Host copy of the head of the control block (status, level count, level sizes).
 struct HostCounters {
     int status;
-    int pad0;
-    u64 count_roots;
-    u64 count_alpha;
+    int n_levels;
+    u64 lvl_m[MAX_LEVELS + 1];
+    u64 lvl_n[MAX_LEVELS + 1];
 };
+static_assert(offsetof(Ctrl, lvl_n) + sizeof(u64) * (MAX_LEVELS + 1) == sizeof(HostCounters),
+              "HostCounters mirrors the head of Ctrl");
 
 int read_counters(const Ctrl *ctrl, HostCounters *h, cudaStream_t s)
 {
@@ -205,8 +215,30 @@ std::vector<int> useful_passes(const u32 (*hist)[RADIX], int n_passes, i64 m)
     return out;
 }
 
+// Worst-case number of contraction levels: a tree of m edges has at most
+// (m - 1) / 2 alpha-edges (Section 4.2), a forest at most m / 2, so level l
+// has at most floor(M / 2^l) edges and the loop ends within
+// ceil(log2(M + 1)) levels.
+int level_bound(i64 M)
+{
+    int L = 0;
+    while (L < MAX_LEVELS && (M >> L) > 0)
+        ++L;
+    return L;
+}
+
+// The whole pipeline on one workspace.
+//   blocking: the host reads the level sizes after every level (exact launch
+//             sizes, loop ends at the first level without alpha-edges, trivial
+//             sort passes skipped) and returns the device status;
+//   !blocking: everything is enqueued for the worst case (level_bound levels,
+//             every sort pass) with no host synchronisation and no allocation,
+//             so the call can be captured in a CUDA graph; kernels of levels
+//             past the last one exit at once.  The device status stays in the
+//             workspace (pandora_workspace_status).
 int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off, i32 *ep,
-        i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s)
+        i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s,
+        bool blocking = true)
 {
     const i64 N = M + T;
     if (stats)
@@ -225,6 +257,8 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     unsigned char *maybe = (unsigned char *)(base + L.maybe);
     i32 *ptr = (i32 *)(base + L.ptr);
     i32 *vmap0 = (i32 *)(base + L.vmap0);
+    i32 *deep = (i32 *)(base + L.deep), *uf = (i32 *)(base + L.uf);
+    i32 *root_of = (i32 *)(base + L.root_of);
     int2 *kept_rec = (int2 *)(base + L.kept_rec);
     int2 *abX = (int2 *)(base + L.abX), *abY = (int2 *)(base + L.abY);
     u32 *erX = (u32 *)(base + L.erX), *erY = (u32 *)(base + L.erY);
@@ -232,14 +266,22 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     i32 *start = (i32 *)(base + L.start);
     int *status = &ctrl->status;
 
-    CallTimer timer(s);
+    CallTimer timer(s, blocking);
+    HostCounters h{};
+    h.lvl_m[0] = (u64)M;
+    h.lvl_n[0] = (u64)N;
+    // control block: zero, then level 0's sizes
     PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    // set by a kernel, not copied from host memory, so that a captured graph
+    // does not depend on host memory that is gone at replay
+    timer.launch(K_FILL, 1, [&] { launch_set_u64_pair(&ctrl->lvl_m[0], (u64)M, &ctrl->lvl_n[0], (u64)N, s); });
     if (d_off)
         timer.launch(K_CHECK_OFFSETS, T + 1, [&] { launch_check_offsets(d_off, T, M, status, s); });
-    HostCounters h{};
     if (M == 0) {
         timer.launch(K_FILL, N, [&] { launch_fill(vp, N, -1, s); });
         PANDORA_CUDA(cudaGetLastError());
+        if (!blocking)
+            return PANDORA_OK;
         if (int e = read_counters(ctrl, &h, s))
             return e;
         return h.status;
@@ -247,19 +289,24 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
 
     // ---- 1. sort by (weight, index) -------------------------------------------
     timer.launch(K_HIST_WEIGHTS, M, [&] { launch_hist_weights(w, M, &ctrl->hist1[0][0], status, s); });
-    static thread_local u32 hhist[4][RADIX];
-    PANDORA_CUDA(cudaMemcpyAsync(hhist, ctrl->hist1, sizeof(hhist), cudaMemcpyDeviceToHost, s));
-    if (int e = read_counters(ctrl, &h, s))
-        return e;
-    if (h.status)
-        return h.status;
-    std::vector<int> passes = useful_passes(hhist, 4, M);
-    if (passes.empty())
-        passes.push_back(3);   // still one pass: it writes the permutation and endpoints
+    std::vector<int> passes = {0, 1, 2, 3};
+    if (blocking) {
+        static thread_local u32 hhist[4][RADIX];
+        PANDORA_CUDA(cudaMemcpyAsync(hhist, ctrl->hist1, sizeof(hhist), cudaMemcpyDeviceToHost, s));
+        if (int e = read_counters(ctrl, &h, s))
+            return e;
+        if (h.status)
+            return h.status;
+        passes = useful_passes(hhist, 4, M);
+        if (passes.empty())
+            passes.push_back(3);   // still one pass: it writes the permutation and endpoints
+    }
     // the endpoint streams ping-pong through arrays that are idle until the
     // level loop: the two halves of kept_rec (>= M entries each), min_word
     // (2N entries) and ptr (N)
-    u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + L.kept_cap;
+    // (pvA starts at a 256-byte boundary: the sort reads these arrays with
+    // bulk copies, which need 16-byte aligned sources)
+    u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + ((L.kept_cap + 63) & ~(i64)63);
     u32 *puB = (u32 *)min_word, *pvB = (u32 *)ptr;
     const u32 *cur_k = nullptr, *cur_v = nullptr, *cur_u = nullptr, *cur_w = nullptr;
     bool toA = false;
@@ -310,34 +357,45 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     PANDORA_CUDA(cudaGetLastError());
 
     // ---- 2. contraction levels ------------------------------------------------
+    const int L_bound = level_bound(M);
     const int2 *ab = ab0;
     const u32 *er = nullptr;
-    i64 m_l = M, n_l = N, kept_used = 0;
+    i64 m_grid = M, n_grid = N, m_cap = M, n_cap = N, kept_used = 0;
     LevelTable table{};
     int n_levels = 0;
     bool useX = true;
-    for (int l = 0;; ++l) {
-        if (l >= MAX_LEVELS)
-            return PANDORA_ERR_ITERATION_LIMIT;
+    for (int l = 0; l < L_bound; ++l) {
         LevelParams P{};
         P.level = l;
-        P.m = m_l;
-        P.n = n_l;
+        P.d_m = &ctrl->lvl_m[l];
+        P.d_n = &ctrl->lvl_n[l];
+        P.d_m_next = &ctrl->lvl_m[l + 1];
+        P.d_n_next = &ctrl->lvl_n[l + 1];
+        P.m_cap = m_cap;
+        P.n_cap = n_cap;
+        P.m_grid = m_grid;
+        P.n_grid = n_grid;
+        P.d_n_levels = &ctrl->n_levels;
         P.ab = ab;
         P.er = er;
         P.min_word = min_word;
         P.maybe = maybe;
         P.ptr = ptr;
+        P.deep = deep;
+        P.uf = uf;
+        P.root_of = root_of;
+        P.d_n_deep = &ctrl->n_deep;
         if (l == 0) {
             P.vmap = vmap0;
             P.perm = perm;
             P.vertex_parent = vp;
         } else {
-            if (kept_used + n_l > L.kept_cap)
-                return PANDORA_ERR_NOT_A_TREE;
+            if (kept_used + n_cap > L.kept_cap)
+                return PANDORA_ERR_NOT_A_TREE;   // only reachable in blocking mode
             P.rec = kept_rec + kept_used;
-            kept_used += n_l;
+            kept_used += n_cap;
             table.rec[l] = P.rec;
+            table.n_cap[l] = n_cap;
         }
         P.edge_off = d_off;
         P.n_trees = T;
@@ -348,48 +406,52 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         P.start = start;
         P.lb = lb;
         P.tile_counter = ctrl->tile_counter;
-        P.count_roots = &ctrl->count_roots;
-        P.count_alpha = &ctrl->count_alpha;
         P.status = status;
-        PANDORA_CUDA(cudaMemsetAsync(min_word, 0xFF, (size_t)n_l * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(
-            lb, 0, (size_t)(level_tiles(n_l) + 1 + level_tiles(m_l) + 1) * 8, s));
+            lb, 0, (size_t)(level_tiles(n_grid) + 1 + level_tiles(m_grid) + 1) * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 8, s));
-        PANDORA_CUDA(cudaMemsetAsync(&ctrl->count_roots, 0, 16, s));
-        timer.launch(K_MARK, m_l, [&] { launch_mark(P, s); });
-        timer.launch(K_PTR_INIT, n_l, [&] { launch_ptr_init(P, s); });
-        timer.launch(K_COMPRESS, n_l, [&] { launch_compress(P, s); });
-        timer.launch(K_COMPACT, m_l, [&] { launch_compact(P, s); });
+        timer.launch(K_INIT_LEVEL, n_grid, [&] { launch_init_level(P, s); });
+        timer.launch(K_MARK, m_grid, [&] { launch_mark(P, s); });
+        timer.launch(K_PTR_INIT, n_grid, [&] { launch_ptr_init(P, s); });
+        timer.launch(K_COMPRESS, n_grid, [&] { launch_compress(P, s); });
+        timer.launch(K_COMPACT, m_grid, [&] { launch_compact(P, s); });
         PANDORA_CUDA(cudaGetLastError());
-        if (int e = read_counters(ctrl, &h, s))
-            return e;
-        if (stats) {
-            stats->level_edges[l] = m_l;
-            stats->level_vertices[l] = n_l;
-            stats->n_levels = l + 1;
-        }
-        if (h.status)
-            return h.status;
         n_levels = l + 1;
-        // every level of a forest of T trees has n_l = m_l + T
-        if ((i64)h.count_roots != (i64)h.count_alpha + T)
-            return PANDORA_ERR_NOT_A_TREE;
-        if (h.count_alpha == 0)
-            break;
-        if ((i64)h.count_alpha > L.half_cap)
-            return PANDORA_ERR_NOT_A_TREE;
         ab = P.ab_next;
         er = P.er_next;
-        m_l = (i64)h.count_alpha;
-        n_l = (i64)h.count_roots;
         useX = !useX;
+        if (blocking) {
+            if (int e = read_counters(ctrl, &h, s))
+                return e;
+            if (stats) {
+                stats->level_edges[l] = (i64)h.lvl_m[l];
+                stats->level_vertices[l] = (i64)h.lvl_n[l];
+                stats->n_levels = l + 1;
+            }
+            if (h.status)
+                return h.status;
+            if (h.n_levels)
+                break;
+            if ((i64)h.lvl_m[l + 1] > L.half_cap)
+                return PANDORA_ERR_NOT_A_TREE;
+            m_grid = m_cap = (i64)h.lvl_m[l + 1];
+            n_grid = n_cap = (i64)h.lvl_n[l + 1];
+        } else {
+            // worst case for the next level (a forest loses at least half its edges)
+            m_cap = m_grid = std::min<i64>(m_cap / 2, L.half_cap);
+            n_cap = n_grid = m_cap + T;
+        }
     }
+    if (blocking && h.n_levels == 0)
+        return PANDORA_ERR_NOT_A_TREE;   // the level bound of Section 4.2 was exceeded
 
     // ---- 3. expansion: chain key of every edge -----------------------------
     const u32 root_base = (u32)(2 * M);
     ExpandParams E{};
     E.m = M;
-    E.n_levels = n_levels;
+    E.max_levels = n_levels;
+    E.d_n_levels = &ctrl->n_levels;
+    E.lvl_n = ctrl->lvl_n;
     E.lev = lev;
     E.start = start;
     E.perm = perm;
@@ -401,18 +463,24 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     E.status = status;
     timer.launch(K_EXPAND, M, [&] { launch_expand(E, table, s); });
     PANDORA_CUDA(cudaGetLastError());
-    PANDORA_CUDA(cudaMemcpyAsync(hhist, ctrl->hist2, sizeof(hhist), cudaMemcpyDeviceToHost, s));
-    if (int e = read_counters(ctrl, &h, s))
-        return e;
-    if (h.status)
-        return h.status;
-
-    // ---- 4. stable sort by chain key, then link -------------------------------
     const u64 max_key = (u64)root_base + (u64)T - 1;
     int bits = 0;
     while (bits < 32 && (max_key >> bits) != 0)
         ++bits;
-    const std::vector<int> passes2 = useful_passes(hhist, (bits + 7) / 8, M);
+    std::vector<int> passes2;
+    for (int q = 0; q < (bits + 7) / 8; ++q)
+        passes2.push_back(q);
+    if (blocking) {
+        static thread_local u32 hhist2[4][RADIX];
+        PANDORA_CUDA(cudaMemcpyAsync(hhist2, ctrl->hist2, sizeof(hhist2), cudaMemcpyDeviceToHost, s));
+        if (int e = read_counters(ctrl, &h, s))
+            return e;
+        if (h.status)
+            return h.status;
+        passes2 = useful_passes(hhist2, (bits + 7) / 8, M);
+    }
+
+    // ---- 4. stable sort by chain key, then link -------------------------------
     const u32 *sk = keysA, *sv = perm;
     for (size_t k = 0; k < passes2.size(); ++k) {
         OnesweepParams P{};
@@ -444,6 +512,8 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     K.n_trees = T;
     timer.launch(K_LINK, M, [&] { launch_link(K, s); });
     PANDORA_CUDA(cudaGetLastError());
+    if (!blocking)
+        return PANDORA_OK;
     if (int e = read_counters(ctrl, &h, s))
         return e;
     return h.status;
@@ -609,6 +679,45 @@ int pandora_profile_read(pandora_profile *out)
         out->total_ms[k] = p.timing ? p.ms[k] : -1.0;
     }
     return PANDORA_OK;
+}
+
+int pandora_dendrogram_async(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                             int32_t *edge_parent, int32_t *vertex_parent, void *workspace,
+                             size_t workspace_bytes, void *stream)
+{
+    if (int e = check_common(u, v, w, n_edges, 1, edge_parent, vertex_parent))
+        return e;
+    return run(u, v, w, n_edges, 1, nullptr, edge_parent, vertex_parent, workspace,
+               workspace_bytes, nullptr, (cudaStream_t)stream, false);
+}
+
+int pandora_dendrogram_batched_async(const int32_t *u, const int32_t *v, const float *w,
+                                     const int64_t *edge_offsets, int64_t n_trees,
+                                     int64_t total_edges, int32_t *edge_parent,
+                                     int32_t *vertex_parent, void *workspace,
+                                     size_t workspace_bytes, void *stream)
+{
+    if (int e = check_common(u, v, w, total_edges, n_trees, edge_parent, vertex_parent))
+        return e;
+    if (n_trees == 0)
+        return total_edges == 0 ? PANDORA_OK : PANDORA_ERR_INVALID_ARGUMENT;
+    if (!edge_offsets)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    return run(u, v, w, total_edges, n_trees, edge_offsets, edge_parent, vertex_parent, workspace,
+               workspace_bytes, nullptr, (cudaStream_t)stream, false);
+}
+
+int pandora_workspace_status(const void *workspace, void *stream)
+{
+    if (!workspace)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    const char *base = (const char *)(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    int status = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&status, base, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PANDORA_ERR_CUDA;
+    return status;
 }
 
 const char *pandora_status_string(int status)

@@ -8,12 +8,16 @@
 // the input is in ascending rank, so every chain comes out in ascending rank.
 //
 // One pass = one kernel (Adinets & Merrill's onesweep): a block takes the
-// next tile id from an atomic counter, ranks its keys by digit with warp
-// ballots (stable: warp w of the tile owns a contiguous run of keys, taken 32
-// at a time in order), publishes its per-digit counts and sums the counts of
-// all earlier tiles by decoupled look-back (eight predecessor tiles per
-// round trip), then scatters keys and each value stream through shared
-// memory so that every digit's run is written contiguously.  The per-pass
+// next tile id from an atomic counter and at once starts TMA bulk copies
+// (cp.async.bulk, completed on mbarriers) of the tile's keys and of every
+// value stream into shared memory; it ranks the keys by digit with warp
+// ballots as soon as they land (stable: warp w of the tile owns a contiguous
+// run of keys, taken 32 at a time in order), publishes its per-digit counts
+// and sums the counts of all earlier tiles by decoupled look-back (eight
+// predecessor tiles per round trip), then writes keys and each value stream
+// through shared memory so that every digit's run is written contiguously.
+// The value copies land while the block ranks and looks back, so no DRAM
+// latency sits between the look-back and the value writes.  The per-pass
 // digit totals come from one histogram read of all keys before the first
 // pass.
 //
@@ -21,6 +25,8 @@
 // moving 8 more bytes per edge through each pass is cheaper than gathering
 // them at random afterwards (a random 4-byte read costs a 64-byte DRAM
 // burst).
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace pandora {
@@ -96,50 +102,120 @@ __global__ void __launch_bounds__(256) hist_weights_kernel(const float *__restri
     }
 }
 
+// Dynamic shared memory of one onesweep block: the input streams of the tile
+// as the TMA lands them (keys; values; u, v), one staging buffer for the
+// digit-ordered output, per-warp digit counts and the digit of each output
+// position.
+template <int FLAGS>
+struct OsSmem {
+    static constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;
+    static constexpr int kBufs = kUV ? 5 : 3;
+    static constexpr size_t kBufBytes = (size_t)OS_TILE * 4;
+    static constexpr size_t kWhist = (size_t)kBufs * kBufBytes;
+    static constexpr size_t kDig = kWhist + (size_t)OS_WARPS * RADIX * 4;
+    static constexpr size_t kBytes = kDig + OS_TILE;
+};
+
 template <int FLAGS>
 __global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(const OnesweepParams p)
 {
     constexpr bool kAB = (FLAGS & OS_LAST_AB) != 0;
     constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;
-    __shared__ u32 s_whist[OS_WARPS][RADIX];   // per-warp digit counts, then offsets
-    __shared__ u32 s_buf[OS_TILE];             // tile in digit order (keys, then values)
-    __shared__ u32 s_buf2[kUV ? OS_TILE : 1];  // v beside u
-    __shared__ u32 s_goff[RADIX];              // global position of local position 0, per digit
-    __shared__ unsigned char s_dig[OS_TILE];   // digit of each local position
+    constexpr bool kGen = (FLAGS & OS_GEN_VALS) != 0;
+    using L = OsSmem<FLAGS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    u32 *B0 = (u32 *)smem;                        // keys in; later values in digit order
+    u32 *B1 = B0 + OS_TILE;                       // values in; later u in digit order
+    u32 *B2 = B1 + OS_TILE;                       // u in (kUV)
+    u32 *B3 = B2 + OS_TILE;                       // v in (kUV)
+    u32 *B4 = kUV ? B3 + OS_TILE : B2;            // keys in digit order; later v
+    u32 (*s_whist)[RADIX] = (u32(*)[RADIX])(smem + L::kWhist);
+    unsigned char *s_dig = smem + L::kDig;
+    __shared__ u32 s_goff[RADIX];                 // global position of local position 0, per digit
     __shared__ u32 s_local_start[RADIX];
     __shared__ u32 s_warp[RADIX / 32];
     __shared__ u32 s_tile;
+    __shared__ __align__(8) u64 s_bar[2];         // [0] keys landed, [1] value streams landed
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < OS_WARPS * RADIX; i += OS_THREADS)
         (&s_whist[0][0])[i] = 0;
-    if (tid == 0)
+    if (tid == 0) {
         s_tile = atomicAdd(p.tile_counter, 1u);
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const u32 tile = s_tile;
+    const i64 tile_base = (i64)tile * OS_TILE;
+    const i64 rem = p.n - tile_base;
+    const int tile_count = rem < OS_TILE ? (int)rem : OS_TILE;
+    // whole 16-byte chunks go by TMA; the last (tile_count % 4) elements of
+    // the array by plain loads (a bulk copy must not read past its end)
+    const int n_bulk = tile_count & ~3;
+    // A bulk copy needs 16-byte aligned source and destination (the smem
+    // buffers are; tile_base * 4 is a multiple of 16 KB).  Each stream whose
+    // base address is not aligned -- possible for caller arrays -- is read
+    // with plain loads instead.
+    const void *ksrc = (FLAGS & OS_KEY_FROM_W) ? (const void *)(p.w_in + tile_base)
+                                               : (const void *)(p.keys_in + tile_base);
+    const void *vsrc = kGen ? nullptr : (const void *)(p.vals_in + tile_base);
+    const void *usrc = !kUV ? nullptr
+                            : kGen ? (const void *)(p.u + tile_base) : (const void *)(p.pu_in + tile_base);
+    const void *wsrc = !kUV ? nullptr
+                            : kGen ? (const void *)(p.v + tile_base) : (const void *)(p.pv_in + tile_base);
+    const bool k_bulk = (((uintptr_t)ksrc) & 15) == 0;
+    const bool v_bulk = !kGen && (((uintptr_t)vsrc) & 15) == 0;
+    const bool uv_bulk = kUV && ((((uintptr_t)usrc | (uintptr_t)wsrc) & 15) == 0);
+    if (tid == 0) {
+        const u32 bytes = (u32)n_bulk * 4;
+        mbar_arrive_expect_tx(&s_bar[0], k_bulk ? bytes : 0u);
+        if (k_bulk && bytes)
+            tma_load_1d(B0, ksrc, bytes, &s_bar[0]);
+        mbar_arrive_expect_tx(&s_bar[1], (v_bulk ? bytes : 0u) + (uv_bulk ? 2u * bytes : 0u));
+        if (bytes) {
+            if (v_bulk)
+                tma_load_1d(B1, vsrc, bytes, &s_bar[1]);
+            if (uv_bulk) {
+                tma_load_1d(B2, usrc, bytes, &s_bar[1]);
+                tma_load_1d(B3, wsrc, bytes, &s_bar[1]);
+            }
+        }
+    }
+    // tails and streams that are not bulk-copied: plain loads into ranges the
+    // copies do not touch
+    for (int i = (k_bulk ? n_bulk : 0) + tid; i < tile_count; i += OS_THREADS)
+        B0[i] = (FLAGS & OS_KEY_FROM_W) ? __float_as_uint(p.w_in[tile_base + i]) : p.keys_in[tile_base + i];
+    if (!kGen)
+        for (int i = (v_bulk ? n_bulk : 0) + tid; i < tile_count; i += OS_THREADS)
+            B1[i] = p.vals_in[tile_base + i];
+    if (kUV) {
+        for (int i = (uv_bulk ? n_bulk : 0) + tid; i < tile_count; i += OS_THREADS) {
+            B2[i] = kGen ? (u32)p.u[tile_base + i] : p.pu_in[tile_base + i];
+            B3[i] = kGen ? (u32)p.v[tile_base + i] : p.pv_in[tile_base + i];
+        }
+    }
     // global start of every digit's bucket (exclusive scan of the pass histogram)
     const u32 bin_base = digit_exclusive_scan(tid < RADIX ? p.hist[tid] : 0u, s_warp);
-    const u32 tile = s_tile;   // published before the scan's barriers
-    const i64 tile_base = (i64)tile * OS_TILE;
-    const i64 warp_base = tile_base + (i64)warp * (32 * OS_ITEMS);
-    const int shift = p.shift;
+    mbar_wait_bounded(&s_bar[0], 0, p.status);
+    __syncthreads();   // plain-loaded tail elements visible to all
 
-    u32 reg[OS_ITEMS];     // keys, later values
-    u32 lpos[OS_ITEMS];    // rank within warp and digit, later local position
-#pragma unroll
-    for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        if (idx < p.n)
-            reg[it] = (FLAGS & OS_KEY_FROM_W) ? weight_key(p.w_in[idx]) : p.keys_in[idx];
-        else
-            reg[it] = 0;
-    }
+    const int wbase = warp * (32 * OS_ITEMS);   // this warp's run inside the tile
+    const int shift = p.shift;
+    auto key_at = [&](int i) -> u32 {
+        const u32 x = B0[i];
+        return (FLAGS & OS_KEY_FROM_W) ? weight_key(__uint_as_float(x)) : x;
+    };
 
     // ---- stable warp-level ranking by digit (ballot multisplit) ------------
+    u32 lpos[OS_ITEMS];    // rank within warp and digit, later local position
     const u32 lt = lanemask_lt();
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        const bool valid = idx < p.n;
-        const u32 d = (reg[it] >> shift) & 255u;
+        const int i = wbase + it * 32 + lane;
+        const bool valid = i < tile_count;
+        const u32 d = valid ? (key_at(i) >> shift) & 255u : 0u;
         u32 peers = __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
@@ -176,14 +252,16 @@ __global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(con
         s_local_start[tid] = local_start;
     __syncthreads();
 
-    // ---- keys into shared memory in digit order ----------------------------
+    // ---- keys into B4 in digit order ------------------------------------------
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        if (idx < p.n) {
-            const u32 d = (reg[it] >> shift) & 255u;
+        const int i = wbase + it * 32 + lane;
+        if (i < tile_count) {
+            const u32 key = key_at(i);
+            const u32 d = (key >> shift) & 255u;
             const u32 pos = s_local_start[d] + s_whist[warp][d] + lpos[it];
-            s_buf[pos] = reg[it];
+            B4[pos] = key;
+            s_dig[pos] = (unsigned char)d;
             lpos[it] = pos;
         }
     }
@@ -195,20 +273,20 @@ __global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(con
             i64 j = (i64)tile - 1;
             u32 spins = 0;
             for (;;) {
-                u64 s[LB_BATCH];
+                u64 sv[LB_BATCH];
 #pragma unroll
                 for (int k = 0; k < LB_BATCH; ++k)
-                    s[k] = (j - k >= 0) ? ld_relaxed(p.lb + (u64)(j - k) * RADIX + tid) : LB_INC;
+                    sv[k] = (j - k >= 0) ? ld_relaxed(p.lb + (u64)(j - k) * RADIX + tid) : LB_INC;
                 int consumed = 0;
                 bool done = false;
 #pragma unroll
                 for (int k = 0; k < LB_BATCH; ++k) {
                     if (done || consumed < k)
                         continue;
-                    const u64 f = s[k] & ~LB_VAL;
+                    const u64 f = sv[k] & ~LB_VAL;
                     if (f == 0)
                         continue;            // not published yet: reload from here
-                    excl += s[k] & LB_VAL;
+                    excl += sv[k] & LB_VAL;
                     consumed = k + 1;
                     if (f == LB_INC)
                         done = true;
@@ -229,94 +307,64 @@ __global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(con
         }
         s_goff[tid] = bin_base + (u32)excl - local_start;   // modulo 2^32
     }
+    mbar_wait_bounded(&s_bar[1], 0, p.status);   // value streams landed
     __syncthreads();
 
-    // ---- write keys, one digit run after another ---------------------------
-    const i64 rem = p.n - tile_base;
-    const int tile_count = rem < OS_TILE ? (int)rem : OS_TILE;
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-        const int j = k * OS_THREADS + tid;
-        if (j < tile_count) {
-            const u32 key = s_buf[j];
-            const u32 d = (key >> shift) & 255u;
-            s_dig[j] = (unsigned char)d;
-            if (FLAGS & OS_WRITE_KEYS)
-                p.keys_out[s_goff[d] + (u32)j] = key;
-        }
+    // ---- write keys (B4); values, stream 0, into B0 in digit order ------------
+    if (FLAGS & OS_WRITE_KEYS) {
+        for (int j = tid; j < tile_count; j += OS_THREADS)
+            p.keys_out[s_goff[s_dig[j]] + (u32)j] = B4[j];
     }
-
-    // ---- value stream 0: caller edge index --------------------------------------
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        reg[it] = idx < p.n ? ((FLAGS & OS_GEN_VALS) ? (u32)idx : p.vals_in[idx]) : 0u;
+        const int i = wbase + it * 32 + lane;
+        if (i < tile_count)
+            B0[lpos[it]] = kGen ? (u32)(tile_base + i) : B1[i];
     }
     __syncthreads();
-#pragma unroll
-    for (int it = 0; it < OS_ITEMS; ++it) {
-        const i64 idx = warp_base + it * 32 + lane;
-        if (idx < p.n)
-            s_buf[lpos[it]] = reg[it];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < OS_ITEMS; ++k) {
-        const int j = k * OS_THREADS + tid;
-        if (j < tile_count)
-            p.vals_out[s_goff[s_dig[j]] + (u32)j] = s_buf[j];
-    }
 
-    // ---- value streams 1, 2: endpoints u, v -----------------------------------
-    if (FLAGS & OS_PAYLOAD_UV) {
-        __syncthreads();
+    // ---- write values (B0); u, v into B1, B4 in digit order -------------------
+    for (int j = tid; j < tile_count; j += OS_THREADS)
+        p.vals_out[s_goff[s_dig[j]] + (u32)j] = B0[j];
+    if (kUV) {
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            u32 *dst = half == 0 ? s_buf : s_buf2;
-#pragma unroll
-            for (int it = 0; it < OS_ITEMS; ++it) {
-                const i64 idx = warp_base + it * 32 + lane;
-                if (idx < p.n) {
-                    u32 x;
-                    if (FLAGS & OS_GEN_VALS) {
-                        // first pass: read the caller's endpoints, validate them and
-                        // turn tree-local ids into forest ids
-                        i32 a = p.u[idx], b = p.v[idx];
-                        i64 nv = p.n_vertices, voff = 0;
-                        if (FLAGS & OS_FOREST) {
-                            const i64 t = tree_of_edge(p.edge_off, p.n_trees, idx);
-                            const i64 e0 = __ldg(p.edge_off + t), e1 = __ldg(p.edge_off + t + 1);
-                            nv = e1 - e0 + 1;
-                            voff = e0 + t;
-                        }
-                        if (a < 0 || (i64)a >= nv || b < 0 || (i64)b >= nv) {
-                            if (half == 0)
-                                set_status(p.status, PANDORA_ERR_VERTEX_OUT_OF_RANGE);
-                            a = 0;
-                            b = 0;
-                        } else if (a == b && half == 0) {
-                            set_status(p.status, PANDORA_ERR_SELF_LOOP);
-                        }
-                        x = (u32)((half == 0 ? a : b) + voff);
-                    } else {
-                        x = half == 0 ? p.pu_in[idx] : p.pv_in[idx];
+        for (int it = 0; it < OS_ITEMS; ++it) {
+            const int i = wbase + it * 32 + lane;
+            if (i < tile_count) {
+                u32 xa = B2[i], xb = B3[i];
+                if (kGen) {
+                    // first pass: validate the caller's endpoints and turn
+                    // tree-local ids into forest ids
+                    i32 a = (i32)xa, b = (i32)xb;
+                    i64 nv = p.n_vertices, voff = 0;
+                    if (FLAGS & OS_FOREST) {
+                        const i64 t = tree_of_edge(p.edge_off, p.n_trees, tile_base + i);
+                        const i64 e0 = __ldg(p.edge_off + t), e1 = __ldg(p.edge_off + t + 1);
+                        nv = e1 - e0 + 1;
+                        voff = e0 + t;
                     }
-                    dst[lpos[it]] = x;
+                    if (a < 0 || (i64)a >= nv || b < 0 || (i64)b >= nv) {
+                        set_status(p.status, PANDORA_ERR_VERTEX_OUT_OF_RANGE);
+                        a = 0;
+                        b = 0;
+                    } else if (a == b) {
+                        set_status(p.status, PANDORA_ERR_SELF_LOOP);
+                    }
+                    xa = (u32)(a + voff);
+                    xb = (u32)(b + voff);
                 }
+                B1[lpos[it]] = xa;
+                B4[lpos[it]] = xb;
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < OS_ITEMS; ++k) {
-            const int j = k * OS_THREADS + tid;
-            if (j < tile_count) {
-                const u32 pos = s_goff[s_dig[j]] + (u32)j;
-                if (kAB) {
-                    p.ab_out[pos] = make_int2((i32)s_buf[j], (i32)s_buf2[j]);
-                } else {
-                    p.pu_out[pos] = s_buf[j];
-                    p.pv_out[pos] = s_buf2[j];
-                }
+        for (int j = tid; j < tile_count; j += OS_THREADS) {
+            const u32 pos = s_goff[s_dig[j]] + (u32)j;
+            if (kAB) {
+                p.ab_out[pos] = make_int2((i32)B1[j], (i32)B4[j]);
+            } else {
+                p.pu_out[pos] = B1[j];
+                p.pv_out[pos] = B4[j];
             }
         }
     }
@@ -337,8 +385,19 @@ void launch_hist_weights(const float *w, i64 n, u32 *hist, int *status, cudaStre
 template <int F>
 static void launch_os(const OnesweepParams &p, cudaStream_t s)
 {
+    constexpr size_t bytes = OsSmem<F>::kBytes;
+    // opt in to more than 48 KB of dynamic shared memory, once per device
+    static std::atomic<unsigned long long> done_mask{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done_mask.load() & bit)) {
+        cudaFuncSetAttribute(onesweep_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bytes);
+        done_mask.fetch_or(bit);
+    }
     const i64 tiles = onesweep_tiles(p.n);
-    onesweep_kernel<F><<<(unsigned)tiles, OS_THREADS, 0, s>>>(p);
+    onesweep_kernel<F><<<(unsigned)tiles, OS_THREADS, bytes, s>>>(p);
 }
 
 void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s)

@@ -65,3 +65,11 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert bl.pandora_dendrogram_batched(null, null, null, null, 3, 10, null, null, null) == 1
     sz = ctypes.c_size_t(0)
     assert bl.pandora_workspace_size(10, 0, ctypes.byref(sz)) == 1
+
+
+def test_noalloc_scratch_holds_the_largest_accepted_input():
+    """pandora_dendrogram_noalloc's static scratch (32 MiB) must hold the
+    workspace of its largest accepted input, PANDORA_NOALLOC_MAX_EDGES."""
+    text = open(os.path.join(ROOT, "include", "pandora.h")).read()
+    max_edges = int(re.search(r"#define PANDORA_NOALLOC_MAX_EDGES (\d+)", text).group(1))
+    assert _binding.workspace_size(max_edges, 1) <= 32 << 20
