@@ -223,3 +223,141 @@ def batch(n_trees: int, lo: int, hi: int, seed: int, families=("rrt", "path_skew
         offsets[t + 1] = offsets[t] + tr.m
     cat = (lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt))
     return Batch(cat(us, np.int32), cat(vs, np.int32), cat(ws, np.float32), offsets, fams)
+
+
+# ---------------------------------------------------------------------------
+# HDBSCAN-shaped trees: mutual-reachability MSTs of Gaussian-mixture points
+# ---------------------------------------------------------------------------
+def gmm_points(n_points: int, seed: int, dim: int = 3, n_comp: int = 32) -> np.ndarray:
+    """Points of an isotropic Gaussian mixture: means uniform in [0, 10]^dim,
+    scales log-uniform in [0.01, 1], mixing weights ~ Dirichlet(1)."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(0.0, 10.0, size=(n_comp, dim))
+    scales = np.exp(rng.uniform(np.log(0.01), np.log(1.0), size=n_comp))
+    mix = rng.dirichlet(np.ones(n_comp))
+    comp = rng.choice(n_comp, size=n_points, p=mix)
+    return means[comp] + rng.standard_normal((n_points, dim)) * scales[comp, None]
+
+
+def core_distances(points: np.ndarray, min_pts: int) -> np.ndarray:
+    """Distance to the min_pts-th nearest point, counting the point itself."""
+    from scipy.spatial import cKDTree
+    d, _ = cKDTree(points).query(points, k=min_pts, workers=-1)
+    return d[:, -1] if min_pts > 1 else np.zeros(len(points))
+
+
+def mr_mst_bruteforce(points: np.ndarray, min_pts: int):
+    """Exact mutual-reachability MST by Prim's algorithm, O(n^2) (small n)."""
+    n = len(points)
+    core = core_distances(points, min_pts)
+    in_tree = np.zeros(n, bool)
+    best = np.full(n, np.inf)
+    link = np.full(n, -1)
+    best[0] = 0.0
+    us, vs, ws = [], [], []
+    for _ in range(n):
+        cand = np.where(in_tree, np.inf, best)
+        x = int(np.argmin(cand))
+        in_tree[x] = True
+        if link[x] >= 0:
+            us.append(link[x])
+            vs.append(x)
+            ws.append(best[x])
+        d = np.sqrt(((points - points[x]) ** 2).sum(axis=1))
+        mr = np.maximum(np.maximum(core, core[x]), d)
+        upd = (~in_tree) & (mr < best)
+        best[upd] = mr[upd]
+        link[upd] = x
+    return np.array(us), np.array(vs), np.array(ws)
+
+
+def mr_knn_mst(points: np.ndarray, min_pts: int, k: int = 32):
+    """Spanning tree of the mutual-reachability graph restricted to k nearest
+    neighbours.
+
+    Weights are max(core(p), core(q), |p - q|) (core counts the point itself,
+    minPts-th neighbour).  The minimum spanning forest of the symmetric k-NN
+    graph (scipy) is computed first; its components are then joined, Boruvka
+    style, by the lightest mutual-reachability edge between each point of a
+    component and its k nearest points of every other component (kd-tree
+    queries).
+    On mixtures of well separated clusters this is the exact mutual-
+    reachability MST except where a lighter non-k-NN edge exists, which the
+    generator does not search for; ``mr_mst_bruteforce`` is the exact O(n^2)
+    construction for small n.
+    """
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components, minimum_spanning_tree
+    from scipy.spatial import cKDTree
+    n = len(points)
+    kk = min(k, n - 1)
+    tree = cKDTree(points)
+    d, idx = tree.query(points, k=kk + 1, workers=-1)
+    core = d[:, min_pts - 1] if min_pts > 1 else np.zeros(n)
+    rows = np.repeat(np.arange(n), kk)
+    cols = idx[:, 1:].reshape(-1)
+    dd = d[:, 1:].reshape(-1)
+    w = np.maximum(np.maximum(core[rows], core[cols]), dd)
+    # symmetric: keep each pair once with its weight
+    lo, hi = np.minimum(rows, cols), np.maximum(rows, cols)
+    key = lo.astype(np.int64) * n + hi
+    key, first = np.unique(key, return_index=True)
+    g = coo_matrix((w[first] + 1e-300, (lo[first], hi[first])), shape=(n, n)).tocsr()
+    f = minimum_spanning_tree(g).tocoo()
+    us, vs, ws = list(f.row), list(f.col), list(f.data - 1e-300)
+    n_comp, label = connected_components(coo_matrix((np.ones(len(us)), (us, vs)), shape=(n, n)),
+                                         directed=False)
+    while n_comp > 1:
+        groups = [np.nonzero(label == c)[0] for c in range(n_comp)]
+        trees = [cKDTree(points[g]) for g in groups]
+        best = []   # per component: (weight, p, q)
+        for c, gc in enumerate(groups):
+            bw, bp, bq = np.inf, -1, -1
+            for e, ge in enumerate(groups):
+                if e == c:
+                    continue
+                kq = min(k, len(ge))
+                dq, iq = trees[e].query(points[gc], k=kq, workers=-1)
+                if kq == 1:
+                    dq, iq = dq[:, None], iq[:, None]
+                q = ge[iq]
+                mr = np.maximum(np.maximum(core[gc][:, None], core[q]), dq)
+                flat = int(np.argmin(mr))
+                jp, jq = divmod(flat, kq)
+                if mr[jp, jq] < bw:
+                    bw, bp, bq = float(mr[jp, jq]), int(gc[jp]), int(q[jp, jq])
+            best.append((bw, bp, bq))
+        parent = np.arange(n_comp)
+
+        def root(x):
+            while parent[x] != x:
+                parent[x] = parent[parent[x]]
+                x = parent[x]
+            return x
+        for bw, bp, bq in sorted(best):
+            a, b = root(label[bp]), root(label[bq])
+            if a != b:
+                parent[max(a, b)] = min(a, b)
+                us.append(bp)
+                vs.append(bq)
+                ws.append(bw)
+        comp_root = np.array([root(c) for c in range(n_comp)])
+        _, label = np.unique(comp_root[label], return_inverse=True)
+        n_comp = int(label.max()) + 1
+    return np.array(us, np.int64), np.array(vs, np.int64), np.array(ws)
+
+
+def hdbscan_tree(n_points: int, seed: int, min_pts: int = 16, method: str = "knn") -> Tree:
+    """Mutual-reachability spanning tree (minPts counts the point itself) of
+    n_points 3-D Gaussian-mixture points, fp32 weights, canonical layout.
+    method "knn": ``mr_knn_mst``; "bruteforce": the exact MST (small n)."""
+    pts = gmm_points(n_points, seed)
+    if method == "bruteforce":
+        a, b, w = mr_mst_bruteforce(pts, min_pts)
+    else:
+        a, b, w = mr_knn_mst(pts, min_pts)
+    rng = np.random.default_rng(seed + 1)
+    u, v, w32, _, _ = _canonical(rng, a.astype(np.int64), b.astype(np.int64),
+                                 w.astype(np.float32), n_points, True)
+    return Tree(u, v, w32, family="hdbscan", meta=dict(n_points=n_points, min_pts=min_pts,
+                                                       seed=seed))

@@ -242,3 +242,32 @@ def test_batched_bad_offsets(pd):
     with pytest.raises(pd.PandoraError) as ei:
         pd.dendrogram_batched(_dev(b.u), _dev(b.v), _dev(b.w), _dev(off))
     assert ei.value.code == 1
+
+
+def test_hdbscan_shaped_tree(pd):
+    """Mutual-reachability spanning tree of 3-D Gaussian-mixture points with
+    minPts = 16: many weights equal a core distance, so ties are common."""
+    t = inputs.hdbscan_tree(200_000, seed=3)
+    ep, vp = assert_parity(pd, t)
+    pins.check_invariants(t.u, t.v, t.w, ep, vp)
+
+
+# ---- full size, in the launch configuration bench.py times ---------------------
+
+@pytest.mark.parametrize("family", ["rrt", "path_skewed"])
+def test_full_size_1e8(pd, family):
+    """n = 10^8 vertices, the benchmark's trees (seeds 1 and 2), called like
+    bench.py (caller workspace, blocking entry point); every output element is
+    compared with the oracle; the path also with its closed form."""
+    n, seed = 100_000_000, (1 if family == "rrt" else 2)
+    t = inputs.rrt(n, seed) if family == "rrt" else inputs.path_skewed(n, seed)
+    ws = torch.empty(pd.workspace_size(t.m), dtype=torch.uint8, device="cuda")
+    ep, vp = run_gpu(pd, t, workspace=ws)
+    del ws
+    torch.cuda.empty_cache()
+    oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
+    np.testing.assert_array_equal(vp, ovp)
+    np.testing.assert_array_equal(ep, oep)
+    if family == "path_skewed":
+        cep, _ = oracle.cartesian_path(t.w[t.path_eid], t.path_eid)
+        np.testing.assert_array_equal(ep, cep)
