@@ -350,6 +350,17 @@ def run_batched(args):
     kern = {k: {"launches": e["launches"] // 2, "ms": e["ms"] / 2}
             for k, e in bprof.items() if e["launches"]}
 
+    # blocking batched calls: small trees one block each, the rest as one forest
+    for _ in range(2):
+        pd.dendrogram_batched(u, v, w, off, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pd.dendrogram_batched(u, v, w, off, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    dispatch_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    tuning = pd.get_tuning()
+
     # one call per tree: blocking calls, then asynchronous calls back to back
     views = []
     for t in range(b.n_trees):
@@ -383,6 +394,8 @@ def run_batched(args):
         "speedup_vs_per_tree_async": per_tree_async_ms / ms,
         "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
         "blocking_kernel_ms": blocking_ms,
+        "blocking_dispatch_ms": dispatch_ms,
+        "small_tree_cutoff": tuning["small_max_edges"],
         "blocking_kernels": kern,
         "levels": bstats["level_edges"],
         "clocks": sampler.summary(),

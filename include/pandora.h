@@ -186,6 +186,41 @@ int pandora_dendrogram_noalloc(const int32_t *u, const int32_t *v, const float *
                                void *stream);
 
 /*
+ * Small trees (process-wide tuning, thread-safe; host only).  The paper has
+ * no counterpart: its method is run unchanged, only the launch shape differs.
+ *
+ * A tree with at most small_max_edges edges is solved by one thread block
+ * that runs every step of Algorithm 1 (sort, contraction levels of Eq. 1 and
+ * Eq. 2, expansion and linking of Section 3.3) in shared memory: one launch
+ * and no DRAM traffic beyond its input and output.  Results are identical to
+ * the multi-kernel pipeline's.  It is used by
+ *   - single-tree calls (blocking, asynchronous and allocation-free) that do
+ *     not ask for statistics, when n_edges <= small_max_edges;
+ *   - batched blocking calls: trees at or under the cutoff go one block per
+ *     tree, grouped by size bucket; the others are packed into one forest for
+ *     the pipeline (this needs a host read of the offsets, which is why
+ *     batched asynchronous calls always take the forest pipeline).
+ * small_threads[k] is the block size (256, 512 or 1024) for trees of
+ * 2^k .. 2^(k+1)-1 edges (bucket 0 also takes empty trees).  small_max_edges
+ * is clamped to PANDORA_SMALL_CAP; 0 disables the solver.  Defaults: 4096
+ * edges and 512 threads in every bucket; measured values come from the
+ * autotuner (paper_2401_06089_gb300/autotune.py).
+ *
+ * set: PANDORA_ERR_INVALID_ARGUMENT for a null pointer, a negative cutoff or
+ * a block size other than 256/512/1024 (nothing changes then).  Calls already
+ * running keep the settings they started with.
+ * get: copies the settings in force; PANDORA_ERR_INVALID_ARGUMENT on null.
+ */
+#define PANDORA_SMALL_CAP 4096
+typedef struct pandora_tuning {
+    int32_t small_max_edges;
+    int32_t small_threads[13];
+} pandora_tuning;
+
+int pandora_set_tuning(const pandora_tuning *tuning);
+int pandora_get_tuning(pandora_tuning *tuning);
+
+/*
  * Optional instrumentation (process-wide, thread-safe, host memory).
  * pandora_profile_start resets the counters of every kernel of the path.  The
  * library always counts launches; with with_timing != 0 it also records a

@@ -12,10 +12,13 @@ from ._binding import (  # noqa: F401
     dendrogram_async,
     dendrogram_batched,
     dendrogram_batched_async,
+    get_tuning,
     library_path,
+    load_tuning,
     profile_read,
     profile_start,
     load_library,
+    set_tuning,
     status_string,
     workspace_size,
     workspace_status,

@@ -30,7 +30,11 @@ STATUS_NAMES = {
     7: "PANDORA_ERR_OUT_OF_MEMORY",
     8: "PANDORA_ERR_CUDA",
     9: "PANDORA_ERR_WORKSPACE_TOO_SMALL",
+    10: "PANDORA_ERR_SIZE_LIMIT",
 }
+
+SMALL_CAP = 4096          # largest tree the single-block solver takes
+SMALL_BUCKETS = 13        # bucket k: trees with 2^k <= m < 2^(k+1) edges (k = 0 also m = 0)
 
 
 class PandoraError(RuntimeError):
@@ -50,6 +54,11 @@ class Profile(ctypes.Structure):
     _fields_ = [("n_kernels", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("name", (ctypes.c_char * 32) * 16), ("launches", ctypes.c_int64 * 16),
                 ("elements", ctypes.c_int64 * 16), ("total_ms", ctypes.c_double * 16)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("small_max_edges", ctypes.c_int32),
+                ("small_threads", ctypes.c_int32 * SMALL_BUCKETS)]
 
 
 def library_path() -> str:
@@ -83,11 +92,13 @@ def load_library():
         lib.pandora_workspace_status.argtypes = [P, P]
         lib.pandora_profile_start.argtypes = [ctypes.c_int]
         lib.pandora_profile_read.argtypes = [P]
+        lib.pandora_set_tuning.argtypes = [P]
+        lib.pandora_get_tuning.argtypes = [P]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
-                     "pandora_workspace_status"):
+                     "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -103,6 +114,45 @@ def workspace_size(total_edges: int, n_trees: int = 1) -> int:
     if st:
         raise PandoraError(st, "pandora_workspace_size")
     return int(out.value)
+
+
+def get_tuning() -> dict:
+    """The process-wide small-tree settings: {"small_max_edges", "small_threads"}."""
+    t = Tuning()
+    st = load_library().pandora_get_tuning(ctypes.byref(t))
+    if st:
+        raise PandoraError(st, "pandora_get_tuning")
+    return {"small_max_edges": int(t.small_max_edges),
+            "small_threads": [int(x) for x in t.small_threads]}
+
+
+def set_tuning(small_max_edges: int | None = None, small_threads=None) -> dict:
+    """Change the small-tree settings (unspecified fields keep their value).
+
+    ``small_max_edges`` is the largest tree (in edges) the single-block solver
+    takes (0 turns it off, at most ``SMALL_CAP``); ``small_threads`` is a list
+    of 13 block sizes (256, 512 or 1024), one per size bucket.  Returns the
+    settings now in force."""
+    cur = get_tuning()
+    t = Tuning()
+    t.small_max_edges = int(cur["small_max_edges"] if small_max_edges is None else small_max_edges)
+    thr = cur["small_threads"] if small_threads is None else list(small_threads)
+    if len(thr) != SMALL_BUCKETS:
+        raise ValueError(f"small_threads needs {SMALL_BUCKETS} entries")
+    for k, x in enumerate(thr):
+        t.small_threads[k] = int(x)
+    st = load_library().pandora_set_tuning(ctypes.byref(t))
+    if st:
+        raise PandoraError(st, "pandora_set_tuning")
+    return get_tuning()
+
+
+def load_tuning(path: str) -> dict:
+    """Apply a tuning file written by ``paper_2401_06089_gb300.autotune``."""
+    import json
+    with open(path) as f:
+        cfg = json.load(f)
+    return set_tuning(cfg.get("small_max_edges"), cfg.get("small_threads"))
 
 
 def profile_start(timing: bool = False) -> None:

@@ -165,6 +165,36 @@ struct LinkParams {
 
 void launch_link(const LinkParams &p, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// small.cu - single-CTA solver (whole method in shared memory, m <= 4096)
+// ---------------------------------------------------------------------------
+struct SmallParams {
+    const i32 *u;
+    const i32 *v;
+    const float *w;
+    i64 m;                 // one tree: its edge count (edge_off == nullptr)
+    const i64 *edge_off;   // batched: per-tree offsets
+    i64 n_trees;
+    const i32 *tree_list;  // batched: the trees this launch takes (block b -> tree_list[b]),
+                           // or nullptr for block b -> tree b
+    i64 cutoff;            // trees with more edges are skipped (forest pipeline)
+    i32 *edge_parent;
+    i32 *vertex_parent;
+    int *status;
+};
+
+int small_tree_capacity();
+// Layout capacity (256, 1024 or 4096 edges) that holds trees of max_edges.
+int small_layout_capacity(i64 max_edges);
+// One block per tree; every tree the launch covers has at most max_edges edges.
+void launch_small(const SmallParams &p, int threads, i64 max_edges, unsigned blocks,
+                  cudaStream_t s);
+void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *off,
+                         const i32 *list, const i64 *coff, i64 n_list, i32 *cu, i32 *cv, float *cw,
+                         cudaStream_t s);
+void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, const i32 *list,
+                          const i64 *coff, i64 n_list, i32 *ep, i32 *vp, cudaStream_t s);
+
 // forest mode: check the offsets (off[0] == 0, non-decreasing, off[T] == M)
 void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, cudaStream_t s);
 // two 64-bit device words set from kernel parameters (graph-capture safe)

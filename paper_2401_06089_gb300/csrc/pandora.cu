@@ -23,11 +23,13 @@ namespace {
 // ---- optional instrumentation (pandora_profile_*) -------------------------
 enum Slot : int {
     K_HIST_WEIGHTS, K_SORT_WEIGHTS, K_MARK, K_PTR_INIT, K_COMPRESS, K_COMPACT, K_EXPAND,
-    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_INIT_LEVEL, K_SLOTS
+    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_INIT_LEVEL, K_SMALL, K_GATHER, K_SLOTS
 };
+static_assert(K_SLOTS <= PANDORA_PROFILE_SLOTS, "profile slots");
 const char *const kSlotNames[K_SLOTS] = {
     "hist_weights", "onesweep_weights", "mark", "ptr_init", "compress", "compact", "expand",
-    "onesweep_chains", "link", "check_offsets", "fill", "init_level"};
+    "onesweep_chains", "link", "check_offsets", "fill", "init_level", "small_tree",
+    "gather_scatter"};
 
 struct Profiler {
     std::mutex mu;
@@ -236,9 +238,9 @@ int level_bound(i64 M)
 //             so the call can be captured in a CUDA graph; kernels of levels
 //             past the last one exit at once.  The device status stays in the
 //             workspace (pandora_workspace_status).
-int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off, i32 *ep,
-        i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s,
-        bool blocking = true)
+int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off,
+             i32 *ep, i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s,
+             bool blocking)
 {
     const i64 N = M + T;
     if (stats)
@@ -248,6 +250,7 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         return PANDORA_ERR_WORKSPACE_TOO_SMALL;
     char *base = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     Ctrl *ctrl = (Ctrl *)(base + L.ctrl);
+    static_assert(sizeof(Ctrl) > 0, "");
     u32 *keysA = (u32 *)(base + L.keysA), *keysB = (u32 *)(base + L.keysB);
     u32 *valsA = (u32 *)(base + L.valsA), *valsB = (u32 *)(base + L.valsB);
     u32 *perm = (u32 *)(base + L.perm);
@@ -519,6 +522,187 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     return h.status;
 }
 
+// ---- small trees: the single-CTA solver and the batched dispatch ------------
+struct Tuning {
+    std::mutex mu;
+    pandora_tuning t{};
+    Tuning()
+    {
+        t.small_max_edges = PANDORA_SMALL_CAP;
+        for (int k = 0; k < 13; ++k)
+            t.small_threads[k] = 512;
+    }
+};
+Tuning &tuning()
+{
+    static Tuning t;
+    return t;
+}
+pandora_tuning tuning_snapshot()
+{
+    Tuning &t = tuning();
+    std::lock_guard<std::mutex> lock(t.mu);
+    return t.t;
+}
+int size_bucket(i64 m)
+{
+    int k = 0;
+    while (k < 12 && (i64(2) << k) <= m)
+        ++k;
+    return k;
+}
+
+// Extra workspace of a batched blocking call: the large trees packed as one
+// forest (inputs and outputs) and the host-built tree lists.
+struct DispatchLayout {
+    size_t cu, cv, cw, cep, cvp, coff, lists, total;
+};
+DispatchLayout dispatch_layout(i64 M, i64 T)
+{
+    DispatchLayout D{};
+    size_t off = 0;
+    auto take = [&](i64 bytes) {
+        const size_t o = off;
+        off = align_up(off + (size_t)std::max<i64>(bytes, 0));
+        return o;
+    };
+    D.cu = take(M * 4);
+    D.cv = take(M * 4);
+    D.cw = take(M * 4);
+    D.cep = take(M * 4);
+    D.cvp = take((M + T) * 4);
+    D.coff = take((T + 1) * 8);
+    D.lists = take(T * 4);
+    D.total = off;
+    return D;
+}
+size_t total_workspace(i64 M, i64 T)
+{
+    const size_t core = make_layout(M, T).total;
+    return T > 1 ? core + dispatch_layout(M, T).total + 256 : core;
+}
+
+int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off, i32 *ep,
+        i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s,
+        bool blocking = true)
+{
+    const pandora_tuning tn = tuning_snapshot();
+    const i64 cutoff = std::min<i64>(tn.small_max_edges, small_tree_capacity());
+    if (!ws || ws_bytes < total_workspace(M, T))
+        return PANDORA_ERR_WORKSPACE_TOO_SMALL;
+    char *base = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    Ctrl *ctrl = (Ctrl *)base;   // the control block heads every layout
+    if (!d_off && !stats && M >= 1 && M <= cutoff) {
+        // one small tree: one block, whole method in shared memory
+        SmallParams P{};
+        P.u = u;
+        P.v = v;
+        P.w = w;
+        P.m = M;
+        P.cutoff = cutoff;
+        P.edge_parent = ep;
+        P.vertex_parent = vp;
+        P.status = &ctrl->status;
+        CallTimer timer(s, blocking);
+        PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+        timer.launch(K_SMALL, M, [&] { launch_small(P, tn.small_threads[size_bucket(M)], M, 1, s); });
+        PANDORA_CUDA(cudaGetLastError());
+        if (!blocking)
+            return PANDORA_OK;
+        int st = 0;
+        PANDORA_CUDA(cudaMemcpyAsync(&st, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PANDORA_CUDA(cudaStreamSynchronize(s));
+        return st;
+    }
+    if (!d_off || !blocking || stats || cutoff <= 0 || M == 0)
+        return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
+
+    // ---- batched, blocking: small trees to the single-CTA solver -------------
+    std::vector<i64> off(T + 1);
+    PANDORA_CUDA(cudaMemcpyAsync(off.data(), d_off, (T + 1) * sizeof(i64), cudaMemcpyDeviceToHost, s));
+    PANDORA_CUDA(cudaStreamSynchronize(s));
+    bool sane = off[0] == 0 && off[T] == M;
+    for (i64 t = 0; t < T && sane; ++t)
+        sane = off[t + 1] >= off[t];
+    if (!sane)   // the pipeline's own check reports it
+        return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
+    std::vector<i32> large, small_by_bucket[13];
+    std::vector<i64> coff(1, 0);
+    for (i64 t = 0; t < T; ++t) {
+        const i64 m = off[t + 1] - off[t];
+        if (m <= cutoff) {
+            small_by_bucket[size_bucket(m)].push_back((i32)t);
+        } else {
+            large.push_back((i32)t);
+            coff.push_back(coff.back() + m);
+        }
+    }
+    if (large.size() == (size_t)T)
+        return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
+    const Layout L = make_layout(M, T);
+    const DispatchLayout D = dispatch_layout(M, T);
+    char *dbase = base + L.total;
+    i32 *cu = (i32 *)(dbase + D.cu), *cv = (i32 *)(dbase + D.cv);
+    float *cw = (float *)(dbase + D.cw);
+    i32 *cep = (i32 *)(dbase + D.cep), *cvp = (i32 *)(dbase + D.cvp);
+    i64 *d_coff = (i64 *)(dbase + D.coff);
+    i32 *d_lists = (i32 *)(dbase + D.lists);
+    // tree lists: large trees first, then the small ones bucket by bucket
+    std::vector<i32> lists(large);
+    std::vector<std::pair<size_t, size_t>> ranges;   // (first, count) per bucket
+    for (int k = 0; k < 13; ++k) {
+        ranges.push_back({lists.size(), small_by_bucket[k].size()});
+        lists.insert(lists.end(), small_by_bucket[k].begin(), small_by_bucket[k].end());
+    }
+    PANDORA_CUDA(cudaMemcpyAsync(d_lists, lists.data(), lists.size() * sizeof(i32),
+                                 cudaMemcpyHostToDevice, s));
+    PANDORA_CUDA(cudaMemcpyAsync(d_coff, coff.data(), coff.size() * sizeof(i64),
+                                 cudaMemcpyHostToDevice, s));
+    const i64 T_L = (i64)large.size(), M_L = coff.back();
+    int st_core = PANDORA_OK;
+    if (T_L > 0) {
+        CallTimer timer(s, blocking);
+        timer.launch(K_GATHER, M_L, [&] {
+            launch_gather_trees(u, v, w, d_off, d_lists, d_coff, T_L, cu, cv, cw, s);
+        });
+        PANDORA_CUDA(cudaGetLastError());
+        // the pipeline resets the control block, so it runs before the small trees
+        st_core = run_core(cu, cv, cw, M_L, T_L, d_coff, cep, cvp, ws, L.total, nullptr, s, true);
+        timer.launch(K_GATHER, M_L, [&] {
+            launch_scatter_trees(cep, cvp, d_off, d_lists, d_coff, T_L, ep, vp, s);
+        });
+    } else {
+        PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    }
+    {
+        CallTimer timer(s, blocking);
+        for (int k = 0; k < 13; ++k) {
+            if (ranges[k].second == 0)
+                continue;
+            SmallParams P{};
+            P.u = u;
+            P.v = v;
+            P.w = w;
+            P.edge_off = d_off;
+            P.n_trees = T;
+            P.tree_list = d_lists + ranges[k].first;
+            P.cutoff = cutoff;
+            P.edge_parent = ep;
+            P.vertex_parent = vp;
+            P.status = &ctrl->status;
+            timer.launch(K_SMALL, (i64)ranges[k].second, [&] {
+                launch_small(P, tn.small_threads[k], std::min<i64>(cutoff, (i64(2) << k) - 1),
+                             (unsigned)ranges[k].second, s);
+            });
+        }
+    }
+    PANDORA_CUDA(cudaGetLastError());
+    int st = 0;
+    PANDORA_CUDA(cudaMemcpyAsync(&st, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PANDORA_CUDA(cudaStreamSynchronize(s));
+    return st_core ? st_core : st;
+}
+
 int check_common(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, i32 *ep, i32 *vp)
 {
     if (M < 0 || T < 0)
@@ -561,7 +745,7 @@ int run_pooled(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i
     cudaMemPool_t pool = library_pool(dev);
     if (!pool)
         return PANDORA_ERR_CUDA;
-    const size_t bytes = make_layout(M, T).total;
+    const size_t bytes = total_workspace(M, T);
     void *ws = nullptr;
     if (cudaMallocFromPoolAsync(&ws, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
@@ -585,7 +769,7 @@ int run_on_workspace(const i32 *u, const i32 *v, const float *w, i64 M, i32 *ep,
     return run(u, v, w, M, 1, nullptr, ep, vp, ws, ws_bytes, nullptr, s);
 }
 
-size_t workspace_bytes(i64 M, i64 T) { return make_layout(M, T).total; }
+size_t workspace_bytes(i64 M, i64 T) { return total_workspace(M, T); }
 
 }  // namespace pandora
 
@@ -597,7 +781,7 @@ int pandora_workspace_size(int64_t total_edges, int64_t n_trees, size_t *bytes)
 {
     if (!bytes || total_edges < 0 || n_trees < 1 || total_edges + n_trees > (i64)INT32_MAX)
         return PANDORA_ERR_INVALID_ARGUMENT;
-    *bytes = make_layout(total_edges, n_trees).total;
+    *bytes = total_workspace(total_edges, n_trees);
     return PANDORA_OK;
 }
 
@@ -718,6 +902,28 @@ int pandora_workspace_status(const void *workspace, void *stream)
         cudaStreamSynchronize(s) != cudaSuccess)
         return PANDORA_ERR_CUDA;
     return status;
+}
+
+int pandora_set_tuning(const pandora_tuning *t)
+{
+    if (!t || t->small_max_edges < 0)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    for (int k = 0; k < 13; ++k)
+        if (t->small_threads[k] != 256 && t->small_threads[k] != 512 && t->small_threads[k] != 1024)
+            return PANDORA_ERR_INVALID_ARGUMENT;
+    Tuning &g = tuning();
+    std::lock_guard<std::mutex> lock(g.mu);
+    g.t = *t;
+    g.t.small_max_edges = std::min<int32_t>(t->small_max_edges, PANDORA_SMALL_CAP);
+    return PANDORA_OK;
+}
+
+int pandora_get_tuning(pandora_tuning *t)
+{
+    if (!t)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    *t = tuning_snapshot();
+    return PANDORA_OK;
 }
 
 const char *pandora_status_string(int status)

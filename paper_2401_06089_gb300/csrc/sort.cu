@@ -106,6 +106,9 @@ __global__ void __launch_bounds__(256) hist_weights_kernel(const float *__restri
 // as the TMA lands them (keys; values; u, v), one staging buffer for the
 // digit-ordered output, per-warp digit counts and the digit of each output
 // position.
+// Blocks per SM: the variants that carry the endpoints need 100 KB of shared
+// memory and fit two per SM; the others (68 KB) fit three, and are compiled
+// for the registers of three.
 template <int FLAGS>
 struct OsSmem {
     static constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;
@@ -117,7 +120,8 @@ struct OsSmem {
 };
 
 template <int FLAGS>
-__global__ void __launch_bounds__(OS_THREADS, OS_MIN_BLOCKS) onesweep_kernel(const OnesweepParams p)
+__global__ void __launch_bounds__(OS_THREADS, (FLAGS & OS_PAYLOAD_UV) ? OS_MIN_BLOCKS : OS_MIN_BLOCKS + 1)
+    onesweep_kernel(const OnesweepParams p)
 {
     constexpr bool kAB = (FLAGS & OS_LAST_AB) != 0;
     constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;

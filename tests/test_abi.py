@@ -73,3 +73,33 @@ def test_noalloc_scratch_holds_the_largest_accepted_input():
     text = open(os.path.join(ROOT, "include", "pandora.h")).read()
     max_edges = int(re.search(r"#define PANDORA_NOALLOC_MAX_EDGES (\d+)", text).group(1))
     assert _binding.workspace_size(max_edges, 1) <= 32 << 20
+
+
+def test_tuning_round_trip_and_validation(lib):
+    """Small-tree settings: defaults, a valid change, rejected changes (host only)."""
+    saved = _binding.get_tuning()
+    try:
+        assert 0 <= saved["small_max_edges"] <= _binding.SMALL_CAP
+        assert len(saved["small_threads"]) == _binding.SMALL_BUCKETS
+        thr = [256, 512, 1024] * 4 + [256]
+        got = _binding.set_tuning(1234, thr)
+        assert got == {"small_max_edges": 1234, "small_threads": thr}
+        assert _binding.set_tuning(10**6)["small_max_edges"] == _binding.SMALL_CAP   # clamped
+        for bad_thr in ([128] * 13, [512] * 12 + [300]):
+            with pytest.raises(_binding.PandoraError) as ei:
+                _binding.set_tuning(100, bad_thr)
+            assert ei.value.code == 1
+        with pytest.raises(_binding.PandoraError):
+            _binding.set_tuning(-1)
+        assert _binding.get_tuning()["small_max_edges"] == _binding.SMALL_CAP   # unchanged
+        assert lib.pandora_set_tuning(None) == 1
+        assert lib.pandora_get_tuning(None) == 1
+    finally:
+        _binding.set_tuning(saved["small_max_edges"], saved["small_threads"])
+
+
+def test_batched_workspace_holds_the_packed_forest():
+    """A batched call's workspace also holds the large trees packed as one forest."""
+    single = _binding.workspace_size(100_000, 1)
+    batched = _binding.workspace_size(100_000, 50)
+    assert batched >= single + 5 * 4 * 100_000
