@@ -16,6 +16,14 @@
 // the heaviest edge of a root chain is the root (-1).
 #include "kernels.cuh"
 
+#ifndef PANDORA_EXPAND_BPS
+#define PANDORA_EXPAND_BPS 16
+#endif
+#ifndef PANDORA_LINK_ITEMS
+#define PANDORA_LINK_ITEMS 4
+#endif
+constexpr int LINK_ITEMS = PANDORA_LINK_ITEMS;
+
 namespace pandora {
 
 namespace {
@@ -95,24 +103,50 @@ __global__ void __launch_bounds__(256) expand_kernel(const ExpandParams p, const
     }
 }
 
+// Section 3.3.3: inside a chain (sorted by rank) an edge's parent is the next
+// edge; the chain's last edge hangs under the chain's head edge, or is the
+// root (-1) for the root chain.  A thread takes LINK_ITEMS edges and issues
+// all loads before its scattered stores, so the random reads of the chain
+// heads overlap.
 template <bool FOREST>
 __global__ void __launch_bounds__(256) link_kernel(const LinkParams p)
 {
-    const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= p.m)
-        return;
-    const u32 k = p.skeys[j];
-    const u32 e = p.svals[j];
-    i32 par;
-    if (j + 1 < p.m && p.skeys[j + 1] == k)
-        par = (i32)p.svals[j + 1];
-    else if (k >= p.root_base)
-        par = -1;
-    else
-        par = (i32)__ldg(p.perm + (k >> 1));
-    if (FOREST && par >= 0)
-        par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, (i64)e));
-    p.edge_parent[e] = par;
+    const i64 tile = (i64)blockIdx.x * 256 * LINK_ITEMS;
+    u32 k[LINK_ITEMS], e[LINK_ITEMS], kn[LINK_ITEMS], en[LINK_ITEMS];
+#pragma unroll
+    for (int it = 0; it < LINK_ITEMS; ++it) {
+        const i64 j = tile + it * 256 + threadIdx.x;
+        k[it] = kn[it] = 0xFFFFFFFFu;
+        e[it] = en[it] = 0;
+        if (j < p.m) {
+            k[it] = p.skeys[j];
+            e[it] = p.svals[j];
+            if (j + 1 < p.m) {
+                kn[it] = p.skeys[j + 1];
+                en[it] = p.svals[j + 1];
+            }
+        }
+    }
+    i32 par[LINK_ITEMS];
+#pragma unroll
+    for (int it = 0; it < LINK_ITEMS; ++it) {
+        if (kn[it] == k[it])
+            par[it] = (i32)en[it];
+        else if (k[it] >= p.root_base)
+            par[it] = -1;
+        else
+            par[it] = (i32)__ldg(p.perm + (k[it] >> 1));
+    }
+#pragma unroll
+    for (int it = 0; it < LINK_ITEMS; ++it) {
+        const i64 j = tile + it * 256 + threadIdx.x;
+        if (j >= p.m)
+            continue;
+        i32 pr = par[it];
+        if (FOREST && pr >= 0)
+            pr -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, (i64)e[it]));
+        p.edge_parent[e[it]] = pr;
+    }
 }
 
 __global__ void check_offsets_kernel(const i64 *off, i64 n_trees, i64 total, int *status)
@@ -148,8 +182,8 @@ void launch_expand(const ExpandParams &p, const LevelTable &t, cudaStream_t s)
     if (p.m <= 0)
         return;
     i64 blocks = (p.m + 256 * 8 - 1) / (256 * 8);
-    if (blocks > 152 * 16)
-        blocks = 152 * 16;
+    if (blocks > 152 * PANDORA_EXPAND_BPS)
+        blocks = 152 * PANDORA_EXPAND_BPS;
     expand_kernel<<<(unsigned)blocks, 256, 0, s>>>(p, t);
 }
 
@@ -157,7 +191,7 @@ void launch_link(const LinkParams &p, cudaStream_t s)
 {
     if (p.m <= 0)
         return;
-    const unsigned blocks = (unsigned)((p.m + 255) / 256);
+    const unsigned blocks = (unsigned)((p.m + 256 * LINK_ITEMS - 1) / (256 * LINK_ITEMS));
     if (p.edge_off)
         link_kernel<true><<<blocks, 256, 0, s>>>(p);
     else

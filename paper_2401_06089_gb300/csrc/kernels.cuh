@@ -95,14 +95,13 @@ struct LevelParams {
     int *d_n_levels;       // Ctrl::n_levels
     const int2 *ab;        // endpoints (level vertex ids), ascending rank
     const u32 *er;         // global rank of each edge (nullptr on level 0: rank = index)
-    u64 *min_word;         // [n] lightest-incident-edge word (see above)
-    unsigned char *maybe;  // [m] bit s: the edge may be the lightest at endpoint s
+    u64 *min_word;         // [n] lightest-incident-edge word (see above); on level 0
+                           // compress swaps its low half for the supervertex
     i32 *ptr;              // [n] pointer forest scratch
     i32 *deep;             // [n] vertices the bounded walk left unresolved (list)
     i32 *uf;               // [n] union-find parents of those vertices
     i32 *root_of;          // [n] dense root id, stored at union-find representatives
     u64 *d_n_deep;         // length of the deep list
-    i32 *vmap;             // [n] vertex -> supervertex (level 0)
     int2 *rec;             // [n] {chain key, supervertex} kept for the expansion (levels >= 1)
     // level 0 only: vertex_parent output
     const u32 *perm;

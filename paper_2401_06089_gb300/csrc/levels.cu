@@ -5,20 +5,22 @@
 // Four kernels process it:
 //
 //   mark      min_word[x] = (rank, other end, side) of the lightest edge at
-//             x (Eq. 1), by 64-bit atomicMin; the value each atomic returns
-//             tells whether the edge can still be the lightest there
+//             x (Eq. 1), by 64-bit atomicMin after a plain read
 //   ptr_init  pointer forest: x points across its lightest edge; the two
 //             endpoints of a leaf edge (lightest at both, Section 3.1) point
 //             at each other and the smaller id becomes the root.  Roots get
 //             dense ids (a single-pass scan) that name the supervertices of
 //             the next level.  On level 0 it also writes the vertex parents
 //             (Eq. 1).
-//   compress  root finding with path halving: supervertex of x, packed on
-//             levels >= 1 with x's chain key for the expansion.
+//   compress  root finding: supervertex of x, kept beside the rank of x's
+//             lightest edge (in x's word on level 0; on levels >= 1 in a
+//             record with x's chain key, kept for the expansion).
 //   compact   alpha-edges (Eq. 2: lightest at neither endpoint) are copied,
 //             in rank order, to the next level with relabelled endpoints;
 //             every other edge is contracted here and records the level and
-//             its supervertex for the expansion.
+//             its supervertex for the expansion.  One random read per
+//             endpoint (rank and supervertex together), the second only when
+//             the edge is not the lightest at the first.
 //
 // The non-alpha edges are exactly the lightest edges {P(x)}, so the components
 // of the pointer forest are the components the paper contracts.  Along a
@@ -101,6 +103,12 @@ __global__ void __launch_bounds__(256) init_level_kernel(const LevelParams p)
         p.min_word[x] = NO_EDGE;
 }
 
+// Blocks per SM of the mark grid.  Fewer random reads and atomics in flight
+// thrash L2 less: at 10^8 edges 3-4 blocks of 256 per SM beat 16 (7.2-7.6 vs
+// 9.2 ms for all levels of a random recursive tree).
+#ifndef PANDORA_MARK_BPS
+#define PANDORA_MARK_BPS 3
+#endif
 template <bool LEVEL0>
 __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
 {
@@ -115,17 +123,11 @@ __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
         const u64 wb = (r << 32) | ((u64)(u32)e.x << 1) | 1u;   // at e.y: other end e.x, side 1
         // A plain read first keeps hub vertices (stars) from serialising on one
         // address: the word only decreases, so a stale read may cost an unneeded
-        // atomic but never a wrong skip.  The value seen (old) decides whether
-        // this edge can still be the lightest at that endpoint.
-        u64 old = p.min_word[e.x];
-        if (old > wa)
-            old = atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
-        const bool maybe_a = old > wa;
-        old = p.min_word[e.y];
-        if (old > wb)
-            old = atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
-        const bool maybe_b = old > wb;
-        p.maybe[i] = (unsigned char)((maybe_a ? 1 : 0) | (maybe_b ? 2 : 0));
+        // atomic but never a wrong skip.
+        if (p.min_word[e.x] > wa)
+            atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
+        if (p.min_word[e.y] > wb)
+            atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
     }
 }
 
@@ -222,11 +224,16 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
 //    log(depth) rounds per vertex.
 constexpr int WALK_STEPS = 8;
 
+// Level 0 keeps the supervertex in the low half of x's own word (the rank
+// of x's lightest edge stays in the high half), so that compact learns both
+// from one random read; higher levels keep {chain key, supervertex} records
+// for the expansion, which carry the rank as well (chain key >> 1).
 template <bool LEVEL0>
 __device__ __forceinline__ void write_supervertex(const LevelParams &p, i64 x, i32 dense)
 {
     if (LEVEL0) {
-        p.vmap[x] = dense;
+        const u64 wx = p.min_word[x];
+        p.min_word[x] = (wx & 0xFFFFFFFF00000000ull) | (u32)dense;
     } else {
         const u64 wx = p.min_word[x];
         const u32 ck = wx == NO_EDGE ? NONE : 2u * (u32)(wx >> 32) + (u32)(wx & 1u);
@@ -391,21 +398,44 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
                 continue;
             const int2 e = p.ab[i];
             const u32 r = LEVEL0 ? (u32)i : p.er[i];
-            const unsigned mb = p.maybe[i];
             rr[it] = r;
-            // Eq. 2: an alpha-edge is the lightest incident edge of neither endpoint
-            const bool a_min = (mb & 1) && (u32)(p.min_word[e.x] >> 32) == r;
-            const bool b_min = (mb & 2) && (u32)(p.min_word[e.y] >> 32) == r;
-            const i32 va = LEVEL0 ? p.vmap[e.x] : p.rec[e.x].y;
-            if (!a_min && !b_min) {
-                const i32 vb = LEVEL0 ? p.vmap[e.y] : p.rec[e.y].y;
+            // Eq. 2: an alpha-edge is the lightest incident edge of neither
+            // endpoint.  One read per endpoint gives the rank of its lightest
+            // edge and its supervertex; the second endpoint is read only when
+            // the edge is not the lightest at the first.
+            u32 rank_a, rank_b;
+            i32 va, vb;
+            if (LEVEL0) {
+                const u64 wa = p.min_word[e.x];
+                rank_a = (u32)(wa >> 32);
+                va = (i32)(u32)wa;
+            } else {
+                const int2 ra = p.rec[e.x];
+                rank_a = (u32)ra.x >> 1;
+                va = ra.y;
+            }
+            if (rank_a == r) {
+                p.lev[r] = (unsigned char)p.level;
+                p.start[r] = va;
+                continue;
+            }
+            if (LEVEL0) {
+                const u64 wb = p.min_word[e.y];
+                rank_b = (u32)(wb >> 32);
+                vb = (i32)(u32)wb;
+            } else {
+                const int2 rb = p.rec[e.y];
+                rank_b = (u32)rb.x >> 1;
+                vb = rb.y;
+            }
+            if (rank_b == r) {
+                p.lev[r] = (unsigned char)p.level;
+                p.start[r] = vb;   // the edge is contracted: same supervertex as e.x
+            } else {
                 if (va == vb)
                     set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // a cycle closed up
                 alpha[it] = true;
                 nab[it] = make_int2(va, vb);
-            } else {
-                p.lev[r] = (unsigned char)p.level;
-                p.start[r] = va;
             }
         }
         u32 rank[LV_ITEMS];
@@ -440,14 +470,19 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
 
 }  // namespace
 
-// Blocks for n elements at per_block each, capped at a few waves of the 152
-// SMs: every level kernel loops (grid-stride or over claimed tiles), so a
+// Blocks for n elements at per_block each, capped at PANDORA_LV_BPS blocks
+// per SM: every level kernel loops (grid-stride or over claimed tiles), so a
 // grid sized for a worst-case bound does not launch idle blocks by the
-// million.
+// million.  The level kernels are bound by random DRAM reads, which more
+// blocks in flight do not speed up; on a 10^8-vertex path the union-find
+// part ran 20% faster at 4 blocks per SM than at 16.
+#ifndef PANDORA_LV_BPS
+#define PANDORA_LV_BPS 4
+#endif
 static unsigned grid_for(i64 n, int per_block)
 {
     i64 b = (n + per_block - 1) / per_block;
-    const i64 cap = 152 * 16;
+    const i64 cap = 152 * PANDORA_LV_BPS;
     if (b > cap)
         b = cap;
     return (unsigned)(b < 1 ? 1 : b);
@@ -463,7 +498,10 @@ void launch_init_level(const LevelParams &p, cudaStream_t s)
 
 void launch_mark(const LevelParams &p, cudaStream_t s)
 {
-    const unsigned blocks = grid_for(p.m_grid, 256);
+    i64 b = (p.m_grid + 255) / 256;
+    if (b > 152 * PANDORA_MARK_BPS)
+        b = 152 * PANDORA_MARK_BPS;
+    const unsigned blocks = (unsigned)(b < 1 ? 1 : b);
     if (p.level == 0)
         mark_kernel<true><<<blocks, 256, 0, s>>>(p);
     else

@@ -129,7 +129,7 @@ class CallTimer {
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, maybe, ptr, vmap0;
+    size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, ptr;
     size_t deep, uf, root_of;
     size_t kept_rec, abX, erX, abY, erY, lev, start, total;
     i64 kept_cap, half_cap, lb_words;
@@ -157,9 +157,7 @@ Layout make_layout(i64 M, i64 T)
     L.lb_words = std::max(os_words, lv_words);
     L.lb = take(L.lb_words * 8);
     L.min_word = take(N * 8);
-    L.maybe = take(M);
     L.ptr = take(N * 4);
-    L.vmap0 = take(N * 4);
     L.deep = take(N * 4);
     L.uf = take(N * 4);
     L.root_of = take(N * 4);
@@ -257,9 +255,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     int2 *ab0 = (int2 *)(base + L.ab0);
     u64 *lb = (u64 *)(base + L.lb);
     u64 *min_word = (u64 *)(base + L.min_word);
-    unsigned char *maybe = (unsigned char *)(base + L.maybe);
     i32 *ptr = (i32 *)(base + L.ptr);
-    i32 *vmap0 = (i32 *)(base + L.vmap0);
     i32 *deep = (i32 *)(base + L.deep), *uf = (i32 *)(base + L.uf);
     i32 *root_of = (i32 *)(base + L.root_of);
     int2 *kept_rec = (int2 *)(base + L.kept_rec);
@@ -382,14 +378,12 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         P.ab = ab;
         P.er = er;
         P.min_word = min_word;
-        P.maybe = maybe;
         P.ptr = ptr;
         P.deep = deep;
         P.uf = uf;
         P.root_of = root_of;
         P.d_n_deep = &ctrl->n_deep;
         if (l == 0) {
-            P.vmap = vmap0;
             P.perm = perm;
             P.vertex_parent = vp;
         } else {
