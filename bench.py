@@ -168,7 +168,7 @@ def sort_weight_bytes(m, launches):
 
 
 # per element of the kernel's launch size (edges or vertices of the level)
-MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark": 25,
+MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark": 24,
                "ptr_init": 28, "compress": 16, "compact": 35, "expand": 25, "link": 16,
                "check_offsets": 16, "fill": 4}
 
@@ -298,21 +298,45 @@ def run_batched(args):
     ep = torch.empty(m, dtype=torch.int32, device=dev)
     vp = torch.empty(m + b.n_trees, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # warm-up, then capture the batched call once
-    side = torch.cuda.Stream()
-    side.wait_stream(stream)
-    with torch.cuda.stream(side):
-        for _ in range(max(args.warmup, 3)):
+    tuning = pd.get_tuning()
+
+    def call(kind):
+        if kind == "planned":
+            pd.dendrogram_batched_planned(u, v, w, off, b.edge_offsets, ws, (ep, vp))
+        else:
             pd.dendrogram_batched_async(u, v, w, off, ws, (ep, vp))
-    stream.wait_stream(side)
+
+    def capture(kind):
+        # warm-up on a side stream, then capture the batched call once
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(max(args.warmup, 3)):
+                call(kind)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        pd.workspace_status(ws)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            call(kind)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        pd.workspace_status(ws)
+        return graph
+
+    # the forest-only graph, for comparison (not the headline)
+    g_forest = capture("async")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g_forest.replay()
+    ev1.record(stream)
     torch.cuda.synchronize()
-    pd.workspace_status(ws)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        pd.dendrogram_batched_async(u, v, w, off, ws, (ep, vp))
-    for _ in range(2):
-        g.replay()
-    torch.cuda.synchronize()
+    forest_graph_ms = ev0.elapsed_time(ev1) / args.steps
+    del g_forest
+    g = capture("planned")
     gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
     sampler = ClockSampler(gpu_id)
     time.sleep(0.6)
@@ -359,7 +383,6 @@ def run_batched(args):
         pd.dendrogram_batched(u, v, w, off, workspace=ws, out=(ep, vp))
     torch.cuda.synchronize()
     dispatch_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    tuning = pd.get_tuning()
 
     # one call per tree: blocking calls, then asynchronous calls back to back
     views = []
@@ -386,7 +409,9 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": args.workload, "n_trees": b.n_trees, "total_edges": m,
                    "family": spec["desc"], "seed": spec["seed"],
-                   "mode": "one forest, pandora_dendrogram_batched_async captured in a CUDA graph",
+                   "mode": "pandora_dendrogram_batched_planned captured in a CUDA graph "
+                           "(small trees to the single-block solver per size bucket when "
+                           "the split pays, the rest as one forest)",
                    "l2": "inputs larger than L2"},
         "per_tree_blocking_ms": per_tree_blocking_ms,
         "per_tree_async_ms": per_tree_async_ms,
@@ -395,7 +420,8 @@ def run_batched(args):
         "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
         "blocking_kernel_ms": blocking_ms,
         "blocking_dispatch_ms": dispatch_ms,
-        "small_tree_cutoff": tuning["small_max_edges"],
+        "forest_async_graph_ms": forest_graph_ms,
+        "tuning": tuning,
         "blocking_kernels": kern,
         "levels": bstats["level_edges"],
         "clocks": sampler.summary(),

@@ -155,6 +155,33 @@ int pandora_dendrogram_batched_async(const int32_t *u, const int32_t *v, const f
                                      int32_t *vertex_parent, void *workspace,
                                      size_t workspace_bytes, void *stream);
 
+/*
+ * Asynchronous batched call for a caller that also holds the offsets in host
+ * memory (host_edge_offsets: n_trees + 1 values equal to edge_offsets; read
+ * during the call only).  With them the library splits the batch without a
+ * host synchronisation: trees of at most small_max_edges edges (see
+ * pandora_set_tuning) go to the single-block solver, one block per tree and
+ * one launch per size bucket; the others are packed into one forest for the
+ * pipeline and their results copied back.  A batch is split only when its
+ * small trees hold at least split_min_permille of the edges or there are no
+ * large trees (the packing costs about 40 bytes of copies per large-tree
+ * edge); otherwise it runs as pandora_dendrogram_batched_async.  Every launch
+ * has a grid fixed by the host offsets, so the call can be captured in a CUDA
+ * graph and replayed for batches with the same tree sizes.  The device checks
+ * the host plan against edge_offsets; a mismatch is
+ * PANDORA_ERR_INVALID_ARGUMENT in the workspace's status word.
+ * Returns PANDORA_ERR_INVALID_ARGUMENT at once when host_edge_offsets is
+ * null or not a partition of [0, total_edges) (non-decreasing, first 0, last
+ * total_edges); other errors as pandora_dendrogram_batched_async.  Workspace:
+ * pandora_workspace_size(total_edges, n_trees) bytes.
+ */
+int pandora_dendrogram_batched_planned(const int32_t *u, const int32_t *v, const float *w,
+                                       const int64_t *edge_offsets,
+                                       const int64_t *host_edge_offsets, int64_t n_trees,
+                                       int64_t total_edges, int32_t *edge_parent,
+                                       int32_t *vertex_parent, void *workspace,
+                                       size_t workspace_bytes, void *stream);
+
 /* Waits for `stream` and returns the device status word of the last call
  * that used `workspace` (PANDORA_OK when it found no error). */
 int pandora_workspace_status(const void *workspace, void *stream);
@@ -196,25 +223,30 @@ int pandora_dendrogram_noalloc(const int32_t *u, const int32_t *v, const float *
  * the multi-kernel pipeline's.  It is used by
  *   - single-tree calls (blocking, asynchronous and allocation-free) that do
  *     not ask for statistics, when n_edges <= small_max_edges;
- *   - batched blocking calls: trees at or under the cutoff go one block per
- *     tree, grouped by size bucket; the others are packed into one forest for
- *     the pipeline (this needs a host read of the offsets, which is why
- *     batched asynchronous calls always take the forest pipeline).
+ *   - batched blocking calls (which read the offsets back) and
+ *     pandora_dendrogram_batched_planned: trees at or under the cutoff go one
+ *     block per tree, grouped by size bucket; the others are packed into one
+ *     forest for the pipeline, when the small trees hold at least
+ *     split_min_permille per mille of the batch's edges (or all of them).
+ *     pandora_dendrogram_batched_async, which never sees the offsets on the
+ *     host, always takes the forest pipeline.
  * small_threads[k] is the block size (256, 512 or 1024) for trees of
  * 2^k .. 2^(k+1)-1 edges (bucket 0 also takes empty trees).  small_max_edges
  * is clamped to PANDORA_SMALL_CAP; 0 disables the solver.  Defaults: 4096
- * edges and 512 threads in every bucket; measured values come from the
- * autotuner (paper_2401_06089_gb300/autotune.py).
+ * edges, 512 threads in every bucket, 50 per mille; measured values come
+ * from the autotuner (paper_2401_06089_gb300/autotune.py).
  *
- * set: PANDORA_ERR_INVALID_ARGUMENT for a null pointer, a negative cutoff or
- * a block size other than 256/512/1024 (nothing changes then).  Calls already
- * running keep the settings they started with.
+ * set: PANDORA_ERR_INVALID_ARGUMENT for a null pointer, a negative cutoff, a
+ * block size other than 256/512/1024 or split_min_permille outside
+ * [0, 1000] (nothing changes then).  Calls already running keep the settings
+ * they started with.
  * get: copies the settings in force; PANDORA_ERR_INVALID_ARGUMENT on null.
  */
 #define PANDORA_SMALL_CAP 4096
 typedef struct pandora_tuning {
     int32_t small_max_edges;
     int32_t small_threads[13];
+    int32_t split_min_permille;
 } pandora_tuning;
 
 int pandora_set_tuning(const pandora_tuning *tuning);

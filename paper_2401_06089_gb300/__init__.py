@@ -12,6 +12,7 @@ from ._binding import (  # noqa: F401
     dendrogram_async,
     dendrogram_batched,
     dendrogram_batched_async,
+    dendrogram_batched_planned,
     get_tuning,
     library_path,
     load_tuning,

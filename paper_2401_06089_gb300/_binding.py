@@ -58,7 +58,8 @@ class Profile(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("small_max_edges", ctypes.c_int32),
-                ("small_threads", ctypes.c_int32 * SMALL_BUCKETS)]
+                ("small_threads", ctypes.c_int32 * SMALL_BUCKETS),
+                ("split_min_permille", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -89,6 +90,8 @@ def load_library():
         lib.pandora_version.argtypes = []
         lib.pandora_dendrogram_async.argtypes = [P, P, P, I64, P, P, P, SZ, P]
         lib.pandora_dendrogram_batched_async.argtypes = [P, P, P, P, I64, I64, P, P, P, SZ, P]
+        lib.pandora_dendrogram_batched_planned.argtypes = [P, P, P, P, P, I64, I64, P, P, P, SZ,
+                                                           P]
         lib.pandora_workspace_status.argtypes = [P, P]
         lib.pandora_profile_start.argtypes = [ctypes.c_int]
         lib.pandora_profile_read.argtypes = [P]
@@ -98,7 +101,8 @@ def load_library():
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
-                     "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning"):
+                     "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
+                     "pandora_dendrogram_batched_planned"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -123,15 +127,19 @@ def get_tuning() -> dict:
     if st:
         raise PandoraError(st, "pandora_get_tuning")
     return {"small_max_edges": int(t.small_max_edges),
-            "small_threads": [int(x) for x in t.small_threads]}
+            "small_threads": [int(x) for x in t.small_threads],
+            "split_min_permille": int(t.split_min_permille)}
 
 
-def set_tuning(small_max_edges: int | None = None, small_threads=None) -> dict:
+def set_tuning(small_max_edges: int | None = None, small_threads=None,
+               split_min_permille: int | None = None) -> dict:
     """Change the small-tree settings (unspecified fields keep their value).
 
     ``small_max_edges`` is the largest tree (in edges) the single-block solver
     takes (0 turns it off, at most ``SMALL_CAP``); ``small_threads`` is a list
-    of 13 block sizes (256, 512 or 1024), one per size bucket.  Returns the
+    of 13 block sizes (256, 512 or 1024), one per size bucket;
+    ``split_min_permille`` is the share of a batch's edges (per mille) its
+    small trees must hold before a batched call is split.  Returns the
     settings now in force."""
     cur = get_tuning()
     t = Tuning()
@@ -141,6 +149,8 @@ def set_tuning(small_max_edges: int | None = None, small_threads=None) -> dict:
         raise ValueError(f"small_threads needs {SMALL_BUCKETS} entries")
     for k, x in enumerate(thr):
         t.small_threads[k] = int(x)
+    t.split_min_permille = int(cur["split_min_permille"] if split_min_permille is None
+                               else split_min_permille)
     st = load_library().pandora_set_tuning(ctypes.byref(t))
     if st:
         raise PandoraError(st, "pandora_set_tuning")
@@ -152,7 +162,8 @@ def load_tuning(path: str) -> dict:
     import json
     with open(path) as f:
         cfg = json.load(f)
-    return set_tuning(cfg.get("small_max_edges"), cfg.get("small_threads"))
+    return set_tuning(cfg.get("small_max_edges"), cfg.get("small_threads"),
+                      cfg.get("split_min_permille"))
 
 
 def profile_start(timing: bool = False) -> None:
@@ -338,6 +349,36 @@ def dendrogram_batched_async(u, v, w, edge_offsets, workspace, out):
                                                   _ptr(workspace), workspace.numel(), stream)
     if st:
         raise PandoraError(st, "pandora_dendrogram_batched_async")
+
+
+def dendrogram_batched_planned(u, v, w, edge_offsets, host_edge_offsets, workspace, out):
+    """Enqueue ``pandora_dendrogram_batched_planned``: like
+    ``dendrogram_batched_async`` plus a host copy of the offsets (a CPU int64
+    tensor, numpy array or list with the same values), which lets small trees
+    take the single-block solver without a host synchronisation."""
+    import numpy as np
+    torch = _torch()
+    lib = load_library()
+    _check(w, torch.float32, "w")
+    dev = w.device
+    m = w.numel()
+    _check(u, torch.int32, "u", dev, m)
+    _check(v, torch.int32, "v", dev, m)
+    _check(edge_offsets, torch.int64, "edge_offsets", dev)
+    n_trees = edge_offsets.numel() - 1
+    h = np.ascontiguousarray(np.asarray(host_edge_offsets, dtype=np.int64))
+    if h.shape != (n_trees + 1,):
+        raise ValueError("host_edge_offsets must have n_trees + 1 entries")
+    ep, vp = out
+    _check(ep, torch.int32, "edge_parent", dev, m)
+    _check(vp, torch.int32, "vertex_parent", dev, m + n_trees)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_dendrogram_batched_planned(
+            _ptr(u), _ptr(v), _ptr(w), _ptr(edge_offsets), h.ctypes.data, n_trees, m, _ptr(ep),
+            _ptr(vp), _ptr(workspace), workspace.numel(), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram_batched_planned")
 
 
 def workspace_status(workspace, raise_on_error: bool = True) -> int:

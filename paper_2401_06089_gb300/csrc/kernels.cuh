@@ -177,6 +177,7 @@ struct SmallParams {
     const i32 *tree_list;  // batched: the trees this launch takes (block b -> tree_list[b]),
                            // or nullptr for block b -> tree b
     i64 cutoff;            // trees with more edges are skipped (forest pipeline)
+    i64 total_edges;       // batched: edges of the whole batch (bounds every tree)
     i32 *edge_parent;
     i32 *vertex_parent;
     int *status;
@@ -188,11 +189,51 @@ int small_layout_capacity(i64 max_edges);
 // One block per tree; every tree the launch covers has at most max_edges edges.
 void launch_small(const SmallParams &p, int threads, i64 max_edges, unsigned blocks,
                   cudaStream_t s);
-void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *off,
-                         const i32 *list, const i64 *coff, i64 n_list, i32 *cu, i32 *cv, float *cw,
-                         cudaStream_t s);
-void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, const i32 *list,
-                          const i64 *coff, i64 n_list, i32 *ep, i32 *vp, cudaStream_t s);
+// Size classes of a batched call: 0..12 = single-block buckets (2^k <= m <
+// 2^(k+1); bucket 0 also takes m = 0), 13 = trees for the forest pipeline.
+constexpr int N_CLASSES = 14;
+constexpr int CLASS_LARGE = 13;
+__host__ __device__ inline int size_class(i64 m, i64 cutoff)
+{
+    if (m > cutoff)
+        return CLASS_LARGE;
+    int k = 0;
+    while (k < 12 && (i64(2) << k) <= m)
+        ++k;
+    return k;
+}
+
+// The device half of a plan the host made from its copy of the offsets:
+// tree lists per class (large trees first, then bucket 0, 1, ...) and the
+// packed offsets of the large trees.  The host's counts are checked against
+// the device offsets; a mismatch is PANDORA_ERR_INVALID_ARGUMENT and leaves
+// lists and offsets that stay inside their buffers.
+struct PlanParams {
+    const i64 *off;
+    i64 n_trees;
+    i64 total_edges;
+    i64 cutoff;
+    i32 *lists;                // [n_trees]
+    i64 *coff;                 // [count[CLASS_LARGE] + 1]
+    int *status;
+    i64 base[N_CLASSES];       // first list slot of each class
+    i64 count[N_CLASSES];      // trees of each class (host plan)
+    i64 m_large;               // edges of the large trees (host plan)
+};
+void launch_plan(const PlanParams &p, cudaStream_t s);
+// *to gets *from when *from holds an error (a plan error is the cause of
+// whatever the kernels that followed it found).
+void launch_merge_status(const int *from, int *to, cudaStream_t s);
+
+// Packs the large trees (lists[0, n_list)) into one forest with offsets coff,
+// and copies that forest's outputs back.  Trees whose sizes disagree with
+// the packed offsets are skipped.
+void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *off, i64 n_trees,
+                         i64 total, const i32 *list, const i64 *coff, i64 n_list, i64 packed_total,
+                         i32 *cu, i32 *cv, float *cw, cudaStream_t s);
+void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, i64 n_trees, i64 total,
+                          const i32 *list, const i64 *coff, i64 n_list, i64 packed_total, i32 *ep,
+                          i32 *vp, cudaStream_t s);
 
 // forest mode: check the offsets (off[0] == 0, non-decreasing, off[T] == M)
 void launch_check_offsets(const i64 *off, i64 n_trees, i64 total, int *status, cudaStream_t s);

@@ -525,6 +525,7 @@ struct Tuning {
         t.small_max_edges = PANDORA_SMALL_CAP;
         for (int k = 0; k < 13; ++k)
             t.small_threads[k] = 512;
+        t.split_min_permille = 50;
     }
 };
 Tuning &tuning()
@@ -538,18 +539,13 @@ pandora_tuning tuning_snapshot()
     std::lock_guard<std::mutex> lock(t.mu);
     return t.t;
 }
-int size_bucket(i64 m)
-{
-    int k = 0;
-    while (k < 12 && (i64(2) << k) <= m)
-        ++k;
-    return k;
-}
-
-// Extra workspace of a batched blocking call: the large trees packed as one
-// forest (inputs and outputs) and the host-built tree lists.
+// Extra workspace of a split batched call.  The plan part (tree lists,
+// packed offsets, the plan's status word) is needed by every split; the
+// packed forest (inputs and outputs of the large trees) only when the batch
+// has large trees, which takes two or more trees.
 struct DispatchLayout {
-    size_t cu, cv, cw, cep, cvp, coff, lists, total;
+    size_t lists, coff, dstat, plan_total;
+    size_t cu, cv, cw, cep, cvp, total;
 };
 DispatchLayout dispatch_layout(i64 M, i64 T)
 {
@@ -560,20 +556,152 @@ DispatchLayout dispatch_layout(i64 M, i64 T)
         off = align_up(off + (size_t)std::max<i64>(bytes, 0));
         return o;
     };
+    D.lists = take(T * 4);
+    D.coff = take((T + 1) * 8);
+    D.dstat = take(4);
+    D.plan_total = off;
     D.cu = take(M * 4);
     D.cv = take(M * 4);
     D.cw = take(M * 4);
     D.cep = take(M * 4);
     D.cvp = take((M + T) * 4);
-    D.coff = take((T + 1) * 8);
-    D.lists = take(T * 4);
     D.total = off;
     return D;
 }
+// Workspace of a call with M edges in T trees (what pandora_workspace_size
+// reports): the pipeline's layout, then the dispatch part a batched call may
+// need (a single-tree batch can only split into the single-block solver).
 size_t total_workspace(i64 M, i64 T)
 {
-    const size_t core = make_layout(M, T).total;
-    return T > 1 ? core + dispatch_layout(M, T).total + 256 : core;
+    const DispatchLayout D = dispatch_layout(M, T);
+    return make_layout(M, T).total + (T > 1 ? D.total : D.plan_total) + 256;
+}
+
+bool offsets_partition(const i64 *h_off, i64 T, i64 M)
+{
+    if (h_off[0] != 0 || h_off[T] != M)
+        return false;
+    for (i64 t = 0; t < T; ++t)
+        if (h_off[t + 1] < h_off[t])
+            return false;
+    return true;
+}
+
+// A batched call whose offsets the host also holds (h_off, a partition of
+// [0, M)).  Every tree at or under the cutoff goes to the single-block
+// solver, one block per tree and one launch per size bucket; the others are
+// packed into one forest for the pipeline and copied back.  The packing costs
+// about 40 sequential bytes per large-tree edge, so a batch is only split when
+// its small trees hold at least split_min_permille of the edges (or there are
+// no large trees).  Every launch has a host-known grid: with blocking == false
+// nothing waits on the device and the call can be captured in a graph.
+int run_planned(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off,
+                const i64 *h_off, i32 *ep, i32 *vp, void *ws, size_t ws_bytes, cudaStream_t s,
+                bool blocking, const pandora_tuning &tn)
+{
+    const i64 cutoff = std::min<i64>(tn.small_max_edges, small_tree_capacity());
+    if (!ws || ws_bytes < make_layout(M, T).total)
+        return PANDORA_ERR_WORKSPACE_TOO_SMALL;
+    PlanParams plan{};
+    i64 m_small = 0;
+    for (i64 t = 0; t < T; ++t) {
+        const i64 m = h_off[t + 1] - h_off[t];
+        const int c = size_class(m, cutoff);
+        ++plan.count[c];
+        if (c == CLASS_LARGE)
+            plan.m_large += m;
+        else
+            m_small += m;
+    }
+    const i64 T_L = plan.count[CLASS_LARGE], M_L = plan.m_large;
+    const Layout L = make_layout(M, T);
+    const DispatchLayout D = dispatch_layout(M, T);
+    const size_t need = L.total + (T_L > 0 ? D.total : D.plan_total) + 256;
+    const bool split = cutoff > 0 && T_L < T && ws_bytes >= need &&
+                       (T_L == 0 || m_small * 1000 >= (i64)tn.split_min_permille * M);
+    if (!split)
+        return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, nullptr, s, blocking);
+
+    char *base = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    Ctrl *ctrl = (Ctrl *)base;   // the control block heads every layout
+    char *dbase = base + L.total;
+    i32 *cu = (i32 *)(dbase + D.cu), *cv = (i32 *)(dbase + D.cv);
+    float *cw = (float *)(dbase + D.cw);
+    i32 *cep = (i32 *)(dbase + D.cep), *cvp = (i32 *)(dbase + D.cvp);
+    i64 *coff = (i64 *)(dbase + D.coff);
+    i32 *lists = (i32 *)(dbase + D.lists);
+    int *dstat = (int *)(dbase + D.dstat);
+    // lists: large trees first, then bucket 0, 1, ...
+    plan.base[CLASS_LARGE] = 0;
+    i64 acc = T_L;
+    for (int k = 0; k < CLASS_LARGE; ++k) {
+        plan.base[k] = acc;
+        acc += plan.count[k];
+    }
+    plan.off = d_off;
+    plan.n_trees = T;
+    plan.total_edges = M;
+    plan.cutoff = cutoff;
+    plan.lists = lists;
+    plan.coff = coff;
+    plan.status = dstat;
+    int st_core = PANDORA_OK;
+    {
+        CallTimer timer(s, blocking);
+        PANDORA_CUDA(cudaMemsetAsync(lists, 0xFF, (size_t)T * 4, s));
+        PANDORA_CUDA(cudaMemsetAsync(coff, 0, (size_t)(T + 1) * 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(dstat, 0, 4, s));
+        timer.launch(K_GATHER, T, [&] { launch_plan(plan, s); });
+        if (T_L > 0) {
+            timer.launch(K_GATHER, M_L, [&] {
+                launch_gather_trees(u, v, w, d_off, T, M, lists, coff, T_L, M_L, cu, cv, cw, s);
+            });
+            PANDORA_CUDA(cudaGetLastError());
+        }
+    }
+    if (T_L > 0) {
+        // the pipeline resets the control block, so it runs before the small trees
+        st_core = run_core(cu, cv, cw, M_L, T_L, coff, cep, cvp, ws, L.total, nullptr, s, blocking);
+        if (st_core == PANDORA_ERR_CUDA)
+            return st_core;
+    } else {
+        PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    }
+    {
+        CallTimer timer(s, blocking);
+        if (T_L > 0)
+            timer.launch(K_GATHER, M_L, [&] {
+                launch_scatter_trees(cep, cvp, d_off, T, M, lists, coff, T_L, M_L, ep, vp, s);
+            });
+        for (int k = 0; k < CLASS_LARGE; ++k) {
+            if (plan.count[k] == 0)
+                continue;
+            SmallParams P{};
+            P.u = u;
+            P.v = v;
+            P.w = w;
+            P.edge_off = d_off;
+            P.n_trees = T;
+            P.tree_list = lists + plan.base[k];
+            P.cutoff = cutoff;
+            P.total_edges = M;
+            P.edge_parent = ep;
+            P.vertex_parent = vp;
+            P.status = &ctrl->status;
+            timer.launch(K_SMALL, plan.count[k], [&] {
+                launch_small(P, tn.small_threads[k], std::min<i64>(cutoff, (i64(2) << k) - 1),
+                             (unsigned)plan.count[k], s);
+            });
+        }
+        timer.launch(K_GATHER, 1, [&] { launch_merge_status(dstat, &ctrl->status, s); });
+    }
+    PANDORA_CUDA(cudaGetLastError());
+    if (!blocking)
+        return PANDORA_OK;
+    int st = 0;
+    PANDORA_CUDA(cudaMemcpyAsync(&st, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PANDORA_CUDA(cudaStreamSynchronize(s));
+    return st_core ? st_core : st;
 }
 
 int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off, i32 *ep,
@@ -594,12 +722,15 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
         P.w = w;
         P.m = M;
         P.cutoff = cutoff;
+        P.total_edges = M;
         P.edge_parent = ep;
         P.vertex_parent = vp;
         P.status = &ctrl->status;
         CallTimer timer(s, blocking);
         PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
-        timer.launch(K_SMALL, M, [&] { launch_small(P, tn.small_threads[size_bucket(M)], M, 1, s); });
+        timer.launch(K_SMALL, M, [&] {
+            launch_small(P, tn.small_threads[size_class(M, cutoff)], M, 1, s);
+        });
         PANDORA_CUDA(cudaGetLastError());
         if (!blocking)
             return PANDORA_OK;
@@ -610,91 +741,14 @@ int run(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_o
     }
     if (!d_off || !blocking || stats || cutoff <= 0 || M == 0)
         return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
-
-    // ---- batched, blocking: small trees to the single-CTA solver -------------
-    std::vector<i64> off(T + 1);
-    PANDORA_CUDA(cudaMemcpyAsync(off.data(), d_off, (T + 1) * sizeof(i64), cudaMemcpyDeviceToHost, s));
+    // batched and blocking: read the offsets, then split the batch like a
+    // caller that holds them on the host
+    std::vector<i64> h_off(T + 1);
+    PANDORA_CUDA(cudaMemcpyAsync(h_off.data(), d_off, (T + 1) * sizeof(i64), cudaMemcpyDeviceToHost, s));
     PANDORA_CUDA(cudaStreamSynchronize(s));
-    bool sane = off[0] == 0 && off[T] == M;
-    for (i64 t = 0; t < T && sane; ++t)
-        sane = off[t + 1] >= off[t];
-    if (!sane)   // the pipeline's own check reports it
+    if (!offsets_partition(h_off.data(), T, M))   // the pipeline's own check reports it
         return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
-    std::vector<i32> large, small_by_bucket[13];
-    std::vector<i64> coff(1, 0);
-    for (i64 t = 0; t < T; ++t) {
-        const i64 m = off[t + 1] - off[t];
-        if (m <= cutoff) {
-            small_by_bucket[size_bucket(m)].push_back((i32)t);
-        } else {
-            large.push_back((i32)t);
-            coff.push_back(coff.back() + m);
-        }
-    }
-    if (large.size() == (size_t)T)
-        return run_core(u, v, w, M, T, d_off, ep, vp, ws, ws_bytes, stats, s, blocking);
-    const Layout L = make_layout(M, T);
-    const DispatchLayout D = dispatch_layout(M, T);
-    char *dbase = base + L.total;
-    i32 *cu = (i32 *)(dbase + D.cu), *cv = (i32 *)(dbase + D.cv);
-    float *cw = (float *)(dbase + D.cw);
-    i32 *cep = (i32 *)(dbase + D.cep), *cvp = (i32 *)(dbase + D.cvp);
-    i64 *d_coff = (i64 *)(dbase + D.coff);
-    i32 *d_lists = (i32 *)(dbase + D.lists);
-    // tree lists: large trees first, then the small ones bucket by bucket
-    std::vector<i32> lists(large);
-    std::vector<std::pair<size_t, size_t>> ranges;   // (first, count) per bucket
-    for (int k = 0; k < 13; ++k) {
-        ranges.push_back({lists.size(), small_by_bucket[k].size()});
-        lists.insert(lists.end(), small_by_bucket[k].begin(), small_by_bucket[k].end());
-    }
-    PANDORA_CUDA(cudaMemcpyAsync(d_lists, lists.data(), lists.size() * sizeof(i32),
-                                 cudaMemcpyHostToDevice, s));
-    PANDORA_CUDA(cudaMemcpyAsync(d_coff, coff.data(), coff.size() * sizeof(i64),
-                                 cudaMemcpyHostToDevice, s));
-    const i64 T_L = (i64)large.size(), M_L = coff.back();
-    int st_core = PANDORA_OK;
-    if (T_L > 0) {
-        CallTimer timer(s, blocking);
-        timer.launch(K_GATHER, M_L, [&] {
-            launch_gather_trees(u, v, w, d_off, d_lists, d_coff, T_L, cu, cv, cw, s);
-        });
-        PANDORA_CUDA(cudaGetLastError());
-        // the pipeline resets the control block, so it runs before the small trees
-        st_core = run_core(cu, cv, cw, M_L, T_L, d_coff, cep, cvp, ws, L.total, nullptr, s, true);
-        timer.launch(K_GATHER, M_L, [&] {
-            launch_scatter_trees(cep, cvp, d_off, d_lists, d_coff, T_L, ep, vp, s);
-        });
-    } else {
-        PANDORA_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
-    }
-    {
-        CallTimer timer(s, blocking);
-        for (int k = 0; k < 13; ++k) {
-            if (ranges[k].second == 0)
-                continue;
-            SmallParams P{};
-            P.u = u;
-            P.v = v;
-            P.w = w;
-            P.edge_off = d_off;
-            P.n_trees = T;
-            P.tree_list = d_lists + ranges[k].first;
-            P.cutoff = cutoff;
-            P.edge_parent = ep;
-            P.vertex_parent = vp;
-            P.status = &ctrl->status;
-            timer.launch(K_SMALL, (i64)ranges[k].second, [&] {
-                launch_small(P, tn.small_threads[k], std::min<i64>(cutoff, (i64(2) << k) - 1),
-                             (unsigned)ranges[k].second, s);
-            });
-        }
-    }
-    PANDORA_CUDA(cudaGetLastError());
-    int st = 0;
-    PANDORA_CUDA(cudaMemcpyAsync(&st, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PANDORA_CUDA(cudaStreamSynchronize(s));
-    return st_core ? st_core : st;
+    return run_planned(u, v, w, M, T, d_off, h_off.data(), ep, vp, ws, ws_bytes, s, true, tn);
 }
 
 int check_common(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, i32 *ep, i32 *vp)
@@ -885,6 +939,30 @@ int pandora_dendrogram_batched_async(const int32_t *u, const int32_t *v, const f
                workspace_bytes, nullptr, (cudaStream_t)stream, false);
 }
 
+int pandora_dendrogram_batched_planned(const int32_t *u, const int32_t *v, const float *w,
+                                       const int64_t *edge_offsets,
+                                       const int64_t *host_edge_offsets, int64_t n_trees,
+                                       int64_t total_edges, int32_t *edge_parent,
+                                       int32_t *vertex_parent, void *workspace,
+                                       size_t workspace_bytes, void *stream)
+{
+    if (int e = check_common(u, v, w, total_edges, n_trees, edge_parent, vertex_parent))
+        return e;
+    if (n_trees == 0)
+        return total_edges == 0 ? PANDORA_OK : PANDORA_ERR_INVALID_ARGUMENT;
+    if (!edge_offsets || !host_edge_offsets ||
+        !offsets_partition(host_edge_offsets, n_trees, total_edges))
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (!workspace || workspace_bytes < total_workspace(total_edges, n_trees))
+        return PANDORA_ERR_WORKSPACE_TOO_SMALL;
+    if (total_edges == 0)
+        return run_core(u, v, w, 0, n_trees, edge_offsets, edge_parent, vertex_parent, workspace,
+                        workspace_bytes, nullptr, (cudaStream_t)stream, false);
+    return run_planned(u, v, w, total_edges, n_trees, edge_offsets, host_edge_offsets,
+                       edge_parent, vertex_parent, workspace, workspace_bytes,
+                       (cudaStream_t)stream, false, tuning_snapshot());
+}
+
 int pandora_workspace_status(const void *workspace, void *stream)
 {
     if (!workspace)
@@ -900,7 +978,7 @@ int pandora_workspace_status(const void *workspace, void *stream)
 
 int pandora_set_tuning(const pandora_tuning *t)
 {
-    if (!t || t->small_max_edges < 0)
+    if (!t || t->small_max_edges < 0 || t->split_min_permille < 0 || t->split_min_permille > 1000)
         return PANDORA_ERR_INVALID_ARGUMENT;
     for (int k = 0; k < 13; ++k)
         if (t->small_threads[k] != 256 && t->small_threads[k] != 512 && t->small_threads[k] != 1024)

@@ -134,10 +134,15 @@ __global__ void __launch_bounds__(T) small_tree_kernel(const SmallParams p)
     i64 t = 0;
     if (p.edge_off) {
         t = p.tree_list ? p.tree_list[blockIdx.x] : (i64)blockIdx.x;
-        if (t >= p.n_trees)
-            return;
+        if (t < 0 || t >= p.n_trees)
+            return;   // only after a plan mismatch, which is reported
         e0 = p.edge_off[t];
         m64 = p.edge_off[t + 1] - e0;
+        if (e0 < 0 || m64 < 0 || e0 + m64 > p.total_edges) {
+            if (tid == 0)
+                set_status(p.status, PANDORA_ERR_INVALID_ARGUMENT);
+            return;
+        }
     }
     if (m64 > p.cutoff || m64 > CAP) {
         // the host sends only trees within both bounds
@@ -406,16 +411,21 @@ void launch_small_cap(const SmallParams &p, int threads, unsigned blocks, cudaSt
     }
 }
 
-// Copies the edges of the trees in `list` into a packed forest (compacted
-// offsets `coff`), one block per tree at a time.
+// Copies the edges of the trees in `list` into a packed forest (offsets
+// `coff`), one block per tree at a time.
 __global__ void __launch_bounds__(256) gather_trees_kernel(const i32 *u, const i32 *v, const float *w,
-                                                           const i64 *off, const i32 *list,
-                                                           const i64 *coff, i64 n_list, i32 *cu,
+                                                           const i64 *off, i64 n_trees, i64 total,
+                                                           const i32 *list, const i64 *coff,
+                                                           i64 n_list, i64 packed_total, i32 *cu,
                                                            i32 *cv, float *cw)
 {
     for (i64 k = blockIdx.x; k < n_list; k += gridDim.x) {
         const i64 t = list[k];
+        if (t < 0 || t >= n_trees)
+            continue;
         const i64 e0 = off[t], m = off[t + 1] - e0, c0 = coff[k];
+        if (e0 < 0 || m < 0 || e0 + m > total || c0 < 0 || c0 + m > packed_total)
+            continue;   // only after a plan mismatch, which is reported
         for (i64 j = threadIdx.x; j < m; j += blockDim.x) {
             cu[c0 + j] = u[e0 + j];
             cv[c0 + j] = v[e0 + j];
@@ -427,18 +437,124 @@ __global__ void __launch_bounds__(256) gather_trees_kernel(const i32 *u, const i
 // Copies the packed forest's outputs back to the trees' own positions (ids are
 // tree-local on both sides).
 __global__ void __launch_bounds__(256) scatter_trees_kernel(const i32 *cep, const i32 *cvp,
-                                                            const i64 *off, const i32 *list,
-                                                            const i64 *coff, i64 n_list, i32 *ep,
+                                                            const i64 *off, i64 n_trees, i64 total,
+                                                            const i32 *list, const i64 *coff,
+                                                            i64 n_list, i64 packed_total, i32 *ep,
                                                             i32 *vp)
 {
     for (i64 k = blockIdx.x; k < n_list; k += gridDim.x) {
         const i64 t = list[k];
+        if (t < 0 || t >= n_trees)
+            continue;
         const i64 e0 = off[t], m = off[t + 1] - e0, c0 = coff[k];
+        if (e0 < 0 || m < 0 || e0 + m > total || c0 < 0 || c0 + m > packed_total)
+            continue;
         for (i64 j = threadIdx.x; j < m; j += blockDim.x)
             ep[e0 + j] = cep[c0 + j];
         for (i64 j = threadIdx.x; j <= m; j += blockDim.x)
             vp[e0 + t + j] = cvp[c0 + k + j];
     }
+}
+
+// One block of 1024 threads walks the trees in order, 1024 at a time: per
+// class a warp ballot ranks the trees of the chunk, so every class list keeps
+// tree order (stable), and a warp scan over the large trees' sizes gives
+// their packed offsets.
+__global__ void __launch_bounds__(1024) plan_kernel(const PlanParams p)
+{
+    __shared__ u32 s_cnt[32][N_CLASSES];
+    __shared__ u32 s_tot[N_CLASSES];
+    __shared__ i64 s_run[N_CLASSES];
+    __shared__ i64 s_wm[32];
+    __shared__ i64 s_edges, s_chunk_edges;
+    __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < N_CLASSES)
+        s_run[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        s_edges = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    for (i64 c0 = 0; c0 < p.n_trees; c0 += 1024) {
+        const i64 t = c0 + threadIdx.x;
+        int cls = -1;
+        i64 m = 0;
+        if (t < p.n_trees) {
+            m = p.off[t + 1] - p.off[t];
+            cls = size_class(m < 0 ? p.total_edges + 1 : m, p.cutoff);
+        }
+        u32 my_rank = 0;
+#pragma unroll
+        for (int c = 0; c < N_CLASSES; ++c) {
+            const u32 mask = __ballot_sync(0xFFFFFFFFu, cls == c);
+            if (cls == c)
+                my_rank = __popc(mask & lanemask_lt());
+            if (lane == 0)
+                s_cnt[warp][c] = __popc(mask);
+        }
+        const i64 em = cls == CLASS_LARGE ? m : 0;
+        i64 incl = em;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const i64 y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            s_wm[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x < N_CLASSES) {
+            u32 acc = 0;
+            for (int w = 0; w < 32; ++w) {
+                const u32 x = s_cnt[w][threadIdx.x];
+                s_cnt[w][threadIdx.x] = acc;
+                acc += x;
+            }
+            s_tot[threadIdx.x] = acc;
+        } else if (threadIdx.x == 32) {
+            i64 acc = 0;
+            for (int w = 0; w < 32; ++w) {
+                const i64 x = s_wm[w];
+                s_wm[w] = acc;
+                acc += x;
+            }
+            s_chunk_edges = acc;
+        }
+        __syncthreads();
+        if (cls >= 0) {
+            const i64 pos = s_run[cls] + s_cnt[warp][cls] + my_rank;
+            if (pos < p.count[cls]) {
+                p.lists[p.base[cls] + pos] = (i32)t;
+                if (cls == CLASS_LARGE)
+                    p.coff[pos] = s_edges + s_wm[warp] + incl - em;
+            } else {
+                s_bad = 1;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < N_CLASSES)
+            s_run[threadIdx.x] += s_tot[threadIdx.x];
+        else if (threadIdx.x == 32)
+            s_edges += s_chunk_edges;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bool bad = s_bad != 0 || s_edges != p.m_large;
+        for (int c = 0; c < N_CLASSES; ++c)
+            bad = bad || s_run[c] != p.count[c];
+        if (bad)   // list slots not written keep the host's fill (-1: no tree)
+            set_status(p.status, PANDORA_ERR_INVALID_ARGUMENT);
+        p.coff[p.count[CLASS_LARGE]] = p.m_large;
+    }
+}
+
+// A plan error overrides what the kernels found after it: those ran on a
+// plan the device offsets do not follow.
+__global__ void merge_status_kernel(const int *from, int *to)
+{
+    if (threadIdx.x == 0 && *from != 0)
+        *to = *from;
 }
 
 }  // namespace
@@ -450,23 +566,36 @@ int small_layout_capacity(i64 max_edges)
     return max_edges < 256 ? 256 : max_edges < 1024 ? 1024 : SMALL_CAP;
 }
 
-void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *off,
-                         const i32 *list, const i64 *coff, i64 n_list, i32 *cu, i32 *cv, float *cw,
-                         cudaStream_t s)
+void launch_plan(const PlanParams &p, cudaStream_t s)
 {
-    if (n_list <= 0)
-        return;
-    const unsigned blocks = (unsigned)(n_list < 152 * 16 ? n_list : 152 * 16);
-    gather_trees_kernel<<<blocks, 256, 0, s>>>(u, v, w, off, list, coff, n_list, cu, cv, cw);
+    plan_kernel<<<1, 1024, 0, s>>>(p);
 }
 
-void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, const i32 *list,
-                          const i64 *coff, i64 n_list, i32 *ep, i32 *vp, cudaStream_t s)
+void launch_merge_status(const int *from, int *to, cudaStream_t s)
+{
+    merge_status_kernel<<<1, 32, 0, s>>>(from, to);
+}
+
+void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *off, i64 n_trees,
+                         i64 total, const i32 *list, const i64 *coff, i64 n_list, i64 packed_total,
+                         i32 *cu, i32 *cv, float *cw, cudaStream_t s)
 {
     if (n_list <= 0)
         return;
     const unsigned blocks = (unsigned)(n_list < 152 * 16 ? n_list : 152 * 16);
-    scatter_trees_kernel<<<blocks, 256, 0, s>>>(cep, cvp, off, list, coff, n_list, ep, vp);
+    gather_trees_kernel<<<blocks, 256, 0, s>>>(u, v, w, off, n_trees, total, list, coff, n_list,
+                                               packed_total, cu, cv, cw);
+}
+
+void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, i64 n_trees, i64 total,
+                          const i32 *list, const i64 *coff, i64 n_list, i64 packed_total, i32 *ep,
+                          i32 *vp, cudaStream_t s)
+{
+    if (n_list <= 0)
+        return;
+    const unsigned blocks = (unsigned)(n_list < 152 * 16 ? n_list : 152 * 16);
+    scatter_trees_kernel<<<blocks, 256, 0, s>>>(cep, cvp, off, n_trees, total, list, coff, n_list,
+                                                packed_total, ep, vp);
 }
 
 void launch_small(const SmallParams &p, int threads, i64 max_edges, unsigned blocks,

@@ -342,10 +342,19 @@ __global__ void __launch_bounds__(OS_THREADS, (FLAGS & OS_PAYLOAD_UV) ? OS_MIN_B
                     i32 a = (i32)xa, b = (i32)xb;
                     i64 nv = p.n_vertices, voff = 0;
                     if (FLAGS & OS_FOREST) {
-                        const i64 t = tree_of_edge(p.edge_off, p.n_trees, tile_base + i);
+                        const i64 e = tile_base + i;
+                        const i64 t = tree_of_edge(p.edge_off, p.n_trees, e);
                         const i64 e0 = __ldg(p.edge_off + t), e1 = __ldg(p.edge_off + t + 1);
                         nv = e1 - e0 + 1;
                         voff = e0 + t;
+                        if (e0 < 0 || e1 > p.n || e < e0 || e >= e1) {
+                            // offsets that are not a partition of [0, M) (an
+                            // asynchronous call cannot stop at the host check):
+                            // keep every id inside the forest
+                            set_status(p.status, PANDORA_ERR_INVALID_ARGUMENT);
+                            nv = 0;
+                            voff = 0;
+                        }
                     }
                     if (a < 0 || (i64)a >= nv || b < 0 || (i64)b >= nv) {
                         set_status(p.status, PANDORA_ERR_VERTEX_OUT_OF_RANGE);

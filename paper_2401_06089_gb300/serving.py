@@ -4,11 +4,17 @@ Requests are trees that already live in device memory (for example MSTs
 produced on the GPU).  The server keeps every in-flight batch's inputs,
 scratch and outputs on the device and admits work by HBM footprint:
 
-* ``submit`` queues a request (FIFO);
+* ``submit`` queues a request in one of two FIFO lanes: small requests (at
+  most the single-block solver's cutoff, see ``set_tuning``) and the rest;
 * ``step`` first retires finished batches (CUDA event query), then, while a
-  stream is free, packs the oldest pending requests into one forest -- as
-  many as fit the batch limits and the remaining HBM budget -- and enqueues
-  ``pandora_dendrogram_batched_async`` for it on that stream;
+  stream is free, packs the oldest pending requests of a lane into one
+  forest -- as many as fit the batch limits and the remaining HBM budget --
+  and enqueues ``pandora_dendrogram_batched_planned`` for it on that stream
+  (the server knows every request's size, so the call needs no host
+  synchronisation and a batch of small trees runs entirely in the
+  single-block solver, one block per tree);
+* the small lane goes first and large batches never hold the last free
+  stream, so a small request does not wait behind a batch of large trees;
 * batches on different streams overlap on the device, and requests that
   arrive while others run are admitted as soon as a stream and memory free up.
 
@@ -79,7 +85,7 @@ def batch_footprint(total_edges: int, n_trees: int) -> int:
 class DendrogramServer:
     def __init__(self, hbm_budget_bytes: int, max_batch_edges: int = 32_000_000,
                  max_batch_trees: int = 4096, n_streams: int = 3, device="cuda",
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, small_lane: bool = True):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -88,7 +94,8 @@ class DendrogramServer:
         self.max_batch_trees = int(max_batch_trees)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_streams)]
         self.free_streams = deque(self.streams)
-        self.pending: deque = deque()
+        self.pending: deque = deque()          # large lane
+        self.pending_small: deque = deque()    # small lane
         self.inflight: List[_Batch] = []
         self.bytes_in_use = 0
         self.clock = clock
@@ -96,40 +103,48 @@ class DendrogramServer:
         self.max_inflight = 0
         self.done: List[Result] = []
         B.load_library()
+        self.small_cutoff = B.get_tuning()["small_max_edges"] if small_lane else -1
 
     # -- queue ---------------------------------------------------------------
     def submit(self, req: Request) -> None:
         if req.m > self.max_batch_edges or batch_footprint(req.m, 1) > self.budget:
             raise ValueError(f"request {req.rid} ({req.m} edges) can never fit the server")
-        self.pending.append(req)
+        (self.pending_small if req.m <= self.small_cutoff else self.pending).append(req)
 
     def idle(self) -> bool:
-        return not self.pending and not self.inflight
+        return not self.pending and not self.pending_small and not self.inflight
 
     # -- one scheduling round --------------------------------------------------
     def step(self) -> int:
         """Retire finished batches, admit new ones; returns batches admitted."""
         self.poll()
         admitted = 0
-        while self.pending and self.free_streams:
-            reqs = self._take()
+        while self.free_streams:
+            if self.pending_small:
+                lane = self.pending_small
+            elif self.pending and (len(self.free_streams) > 1 or not self.inflight
+                                   or self.small_cutoff < 0):
+                lane = self.pending   # large batches leave one stream for small requests
+            else:
+                break
+            reqs = self._take(lane)
             if not reqs:
                 break
             self._launch(reqs)
             admitted += 1
         return admitted
 
-    def _take(self) -> List[Request]:
+    def _take(self, lane: deque) -> List[Request]:
         free = self.budget - self.bytes_in_use
         take: List[Request] = []
         m = 0
-        while self.pending and len(take) < self.max_batch_trees:
-            r = self.pending[0]
+        while lane and len(take) < self.max_batch_trees:
+            r = lane[0]
             if m + r.m > self.max_batch_edges:
                 break
             if batch_footprint(m + r.m, len(take) + 1) > free:
                 break
-            take.append(self.pending.popleft())
+            take.append(lane.popleft())
             m += r.m
         return take
 
@@ -152,7 +167,7 @@ class DendrogramServer:
             ws = torch.empty(B.workspace_size(m, max(t, 1)), dtype=torch.uint8, device=self.device)
             ep = torch.empty(m, dtype=torch.int32, device=self.device)
             vp = torch.empty(m + t, dtype=torch.int32, device=self.device)
-            B.dendrogram_batched_async(u, v, w, off, ws, (ep, vp))
+            B.dendrogram_batched_planned(u, v, w, off, offsets, ws, (ep, vp))
             ev = torch.cuda.Event()
             ev.record(stream)
         self.bytes_in_use += fp

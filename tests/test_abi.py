@@ -82,8 +82,8 @@ def test_tuning_round_trip_and_validation(lib):
         assert 0 <= saved["small_max_edges"] <= _binding.SMALL_CAP
         assert len(saved["small_threads"]) == _binding.SMALL_BUCKETS
         thr = [256, 512, 1024] * 4 + [256]
-        got = _binding.set_tuning(1234, thr)
-        assert got == {"small_max_edges": 1234, "small_threads": thr}
+        got = _binding.set_tuning(1234, thr, 75)
+        assert got == {"small_max_edges": 1234, "small_threads": thr, "split_min_permille": 75}
         assert _binding.set_tuning(10**6)["small_max_edges"] == _binding.SMALL_CAP   # clamped
         for bad_thr in ([128] * 13, [512] * 12 + [300]):
             with pytest.raises(_binding.PandoraError) as ei:
@@ -91,11 +91,15 @@ def test_tuning_round_trip_and_validation(lib):
             assert ei.value.code == 1
         with pytest.raises(_binding.PandoraError):
             _binding.set_tuning(-1)
+        for bad_permille in (-1, 1001):
+            with pytest.raises(_binding.PandoraError):
+                _binding.set_tuning(100, None, bad_permille)
         assert _binding.get_tuning()["small_max_edges"] == _binding.SMALL_CAP   # unchanged
         assert lib.pandora_set_tuning(None) == 1
         assert lib.pandora_get_tuning(None) == 1
     finally:
-        _binding.set_tuning(saved["small_max_edges"], saved["small_threads"])
+        _binding.set_tuning(saved["small_max_edges"], saved["small_threads"],
+                            saved["split_min_permille"])
 
 
 def test_batched_workspace_holds_the_packed_forest():
@@ -103,3 +107,22 @@ def test_batched_workspace_holds_the_packed_forest():
     single = _binding.workspace_size(100_000, 1)
     batched = _binding.workspace_size(100_000, 50)
     assert batched >= single + 5 * 4 * 100_000
+
+
+def test_planned_host_offsets_checked_before_any_launch(lib):
+    """The planned batched call rejects host offsets that are not a partition
+    of [0, total_edges), and a missing workspace, before enqueuing anything."""
+    bl = _binding.load_library()
+    null = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(256)   # never dereferenced: the call returns first
+    bad = (ctypes.c_int64 * 4)(0, 5, 3, 10)
+    short = (ctypes.c_int64 * 4)(0, 5, 7, 9)
+    good = (ctypes.c_int64 * 4)(0, 5, 7, 10)
+    args = (fake, fake, fake, fake)
+    for h in (bad, short):
+        assert bl.pandora_dendrogram_batched_planned(*args, h, 3, 10, fake, fake, null, 0,
+                                                      null) == 1
+    assert bl.pandora_dendrogram_batched_planned(*args, null, 3, 10, fake, fake, null, 0,
+                                                  null) == 1
+    assert bl.pandora_dendrogram_batched_planned(*args, good, 3, 10, fake, fake, null, 0,
+                                                  null) == 9

@@ -33,7 +33,7 @@ def pd():
 def tuning(pd):
     saved = pd.get_tuning()
     yield pd
-    pd.set_tuning(saved["small_max_edges"], saved["small_threads"])
+    pd.set_tuning(saved["small_max_edges"], saved["small_threads"], saved["split_min_permille"])
 
 
 def _dev(a):
@@ -214,3 +214,102 @@ def test_async_small_tree_graph(tuning):
     assert pd.workspace_status(ws) == 0
     np.testing.assert_array_equal(ep.cpu().numpy(), oep)
     np.testing.assert_array_equal(vp.cpu().numpy(), ovp)
+
+
+def _planned(pd, b, host_off=None):
+    u, v, w, off = _dev(b.u), _dev(b.v), _dev(b.w), _dev(b.edge_offsets)
+    ws = torch.empty(pd.workspace_size(b.m, b.n_trees), dtype=torch.uint8, device="cuda")
+    ep = torch.empty(b.m, dtype=torch.int32, device="cuda")
+    vp = torch.empty(b.m + b.n_trees, dtype=torch.int32, device="cuda")
+    h = b.edge_offsets if host_off is None else host_off
+    pd.dendrogram_batched_planned(u, v, w, off, h, ws, (ep, vp))
+    st = pd.workspace_status(ws, raise_on_error=False)
+    return st, ep.cpu().numpy(), vp.cpu().numpy()
+
+
+@pytest.mark.parametrize("permille", [0, 50, 1000])
+@pytest.mark.parametrize("cutoff", [0, 300, 4096])
+def test_planned_matches_oracle(tuning, cutoff, permille):
+    """Planned (asynchronous, host offsets) batched calls: split or not, equal
+    to the oracle on a mix around the cutoff and the bucket edges."""
+    pd = tuning
+    pd.set_tuning(cutoff, None, permille)
+    sizes = np.array([1, 2, 3, 40, 299, 300, 301, 302, 1025, 4096, 4097, 4098, 12_000, 1, 9],
+                     np.int64)
+    b = inputs.batch(len(sizes), 1, 1, seed=cutoff + permille, sizes=sizes)
+    oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
+    st, ep, vp = _planned(pd, b)
+    assert st == 0
+    np.testing.assert_array_equal(vp, ovp)
+    np.testing.assert_array_equal(ep, oep)
+
+
+def test_planned_all_small_and_profile(tuning):
+    """A batch of small trees only: no pipeline kernel runs, one solver launch
+    per occupied size bucket."""
+    pd = tuning
+    pd.set_tuning(4096, None, 50)
+    rng = np.random.default_rng(8)
+    sizes = rng.integers(1, 4097, size=300).astype(np.int64)
+    b = inputs.batch(len(sizes), 1, 1, seed=8, sizes=sizes)
+    oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
+    pd.profile_start()
+    st, ep, vp = _planned(pd, b)
+    prof = pd.profile_read()
+    assert st == 0
+    np.testing.assert_array_equal(vp, ovp)
+    np.testing.assert_array_equal(ep, oep)
+    assert prof["mark"]["launches"] == 0
+    buckets = {int(np.floor(np.log2(max(m, 1)))) for m in sizes - 1}
+    assert prof["small_tree"]["launches"] == len(buckets)
+
+
+def test_planned_graph_replay(tuning):
+    """Capture one planned call (split batch) in a CUDA graph and replay it on
+    new batches with the same tree sizes."""
+    pd = tuning
+    pd.set_tuning(4096, None, 0)
+    sizes = inputs.log_uniform_sizes(np.random.default_rng(5), 200, 2, 30_000)
+    batches = [inputs.batch(len(sizes), 0, 0, seed=s, sizes=sizes) for s in (41, 42, 43)]
+    b0 = batches[0]
+    u, v, w, off = _dev(b0.u), _dev(b0.v), _dev(b0.w), _dev(b0.edge_offsets)
+    ws = torch.empty(pd.workspace_size(b0.m, b0.n_trees), dtype=torch.uint8, device="cuda")
+    ep = torch.empty(b0.m, dtype=torch.int32, device="cuda")
+    vp = torch.empty(b0.m + b0.n_trees, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        pd.dendrogram_batched_planned(u, v, w, off, b0.edge_offsets, ws, (ep, vp))
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pd.dendrogram_batched_planned(u, v, w, off, b0.edge_offsets, ws, (ep, vp))
+    for b in batches[1:]:
+        u.copy_(_dev(b.u))
+        v.copy_(_dev(b.v))
+        w.copy_(_dev(b.w))
+        g.replay()
+        torch.cuda.synchronize()
+        assert pd.workspace_status(ws) == 0
+        oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
+        np.testing.assert_array_equal(ep.cpu().numpy(), oep)
+        np.testing.assert_array_equal(vp.cpu().numpy(), ovp)
+
+
+def test_planned_plan_mismatch_is_reported(tuning):
+    """Host offsets that are a partition but not the device's: the device
+    reports PANDORA_ERR_INVALID_ARGUMENT and the library keeps working."""
+    pd = tuning
+    pd.set_tuning(4096, None, 0)
+    sizes = np.array([100, 9000, 50, 7000, 3000], np.int64)
+    b = inputs.batch(len(sizes), 1, 1, seed=12, sizes=sizes)
+    host = b.edge_offsets.copy()
+    host[1] += 5000   # still a partition: tree 0 large and tree 1 small on the host
+    st, _, _ = _planned(pd, b, host_off=host)
+    assert st == 1
+    st, ep, vp = _planned(pd, b)
+    oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
+    assert st == 0
+    np.testing.assert_array_equal(ep, oep)
+    np.testing.assert_array_equal(vp, ovp)
