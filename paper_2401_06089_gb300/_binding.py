@@ -105,7 +105,20 @@ def load_library():
                      "pandora_dendrogram_batched_planned"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
-        return lib
+    _apply_default_tuning()
+    return lib
+
+
+TUNING_FILE = os.path.join(HERE, "tuning_gb300.json")
+
+
+def _apply_default_tuning():
+    """Apply the autotuner's file shipped beside the package (or the file named
+    by PANDORA_TUNING; PANDORA_TUNING=none keeps the library defaults)."""
+    path = os.environ.get("PANDORA_TUNING", TUNING_FILE)
+    if path.lower() == "none" or not os.path.exists(path):
+        return
+    load_tuning(path)
 
 
 def status_string(code: int) -> str:

@@ -412,47 +412,70 @@ void launch_small_cap(const SmallParams &p, int threads, unsigned blocks, cudaSt
 }
 
 // Copies the edges of the trees in `list` into a packed forest (offsets
-// `coff`), one block per tree at a time.
+// `coff`): one thread per packed edge (a binary search over coff finds its
+// tree), so a few large trees still spread over the whole GPU.
 __global__ void __launch_bounds__(256) gather_trees_kernel(const i32 *u, const i32 *v, const float *w,
                                                            const i64 *off, i64 n_trees, i64 total,
                                                            const i32 *list, const i64 *coff,
                                                            i64 n_list, i64 packed_total, i32 *cu,
                                                            i32 *cv, float *cw)
 {
-    for (i64 k = blockIdx.x; k < n_list; k += gridDim.x) {
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < packed_total;
+         j += (i64)gridDim.x * blockDim.x) {
+        const i64 k = tree_of_edge(coff, n_list, j);
         const i64 t = list[k];
         if (t < 0 || t >= n_trees)
-            continue;
-        const i64 e0 = off[t], m = off[t + 1] - e0, c0 = coff[k];
-        if (e0 < 0 || m < 0 || e0 + m > total || c0 < 0 || c0 + m > packed_total)
             continue;   // only after a plan mismatch, which is reported
-        for (i64 j = threadIdx.x; j < m; j += blockDim.x) {
-            cu[c0 + j] = u[e0 + j];
-            cv[c0 + j] = v[e0 + j];
-            cw[c0 + j] = w[e0 + j];
-        }
+        const i64 e0 = off[t], m = off[t + 1] - e0, c0 = coff[k];
+        const i64 i = j - c0;
+        if (e0 < 0 || m < 0 || e0 + m > total || i < 0 || i >= m)
+            continue;
+        cu[j] = u[e0 + i];
+        cv[j] = v[e0 + i];
+        cw[j] = w[e0 + i];
     }
 }
 
 // Copies the packed forest's outputs back to the trees' own positions (ids are
-// tree-local on both sides).
+// tree-local on both sides): one thread per packed edge for edge_parent, one
+// per packed vertex for vertex_parent (packed tree k has vertices
+// [coff[k] + k, coff[k+1] + k + 1)).
 __global__ void __launch_bounds__(256) scatter_trees_kernel(const i32 *cep, const i32 *cvp,
                                                             const i64 *off, i64 n_trees, i64 total,
                                                             const i32 *list, const i64 *coff,
                                                             i64 n_list, i64 packed_total, i32 *ep,
                                                             i32 *vp)
 {
-    for (i64 k = blockIdx.x; k < n_list; k += gridDim.x) {
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x; j < packed_total; j += stride) {
+        const i64 k = tree_of_edge(coff, n_list, j);
         const i64 t = list[k];
         if (t < 0 || t >= n_trees)
             continue;
-        const i64 e0 = off[t], m = off[t + 1] - e0, c0 = coff[k];
-        if (e0 < 0 || m < 0 || e0 + m > total || c0 < 0 || c0 + m > packed_total)
+        const i64 e0 = off[t], m = off[t + 1] - e0, i = j - coff[k];
+        if (e0 < 0 || m < 0 || e0 + m > total || i < 0 || i >= m)
             continue;
-        for (i64 j = threadIdx.x; j < m; j += blockDim.x)
-            ep[e0 + j] = cep[c0 + j];
-        for (i64 j = threadIdx.x; j <= m; j += blockDim.x)
-            vp[e0 + t + j] = cvp[c0 + k + j];
+        ep[e0 + i] = cep[j];
+    }
+    for (i64 x = (i64)blockIdx.x * blockDim.x + threadIdx.x; x < packed_total + n_list;
+         x += stride) {
+        // tree k holds x when coff[k] + k <= x < coff[k + 1] + k + 1
+        i64 lo = 0, hi = n_list - 1;
+        while (lo < hi) {
+            const i64 mid = (lo + hi + 1) >> 1;
+            if (__ldg(coff + mid) + mid <= x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const i64 k = lo;
+        const i64 t = list[k];
+        if (t < 0 || t >= n_trees)
+            continue;
+        const i64 e0 = off[t], m = off[t + 1] - e0, i = x - (coff[k] + k);
+        if (e0 < 0 || m < 0 || e0 + m > total || i < 0 || i > m)
+            continue;
+        vp[e0 + t + i] = cvp[x];
     }
 }
 
@@ -582,7 +605,8 @@ void launch_gather_trees(const i32 *u, const i32 *v, const float *w, const i64 *
 {
     if (n_list <= 0)
         return;
-    const unsigned blocks = (unsigned)(n_list < 152 * 16 ? n_list : 152 * 16);
+    const i64 b = (packed_total + 255) / 256;
+    const unsigned blocks = (unsigned)(b < 1 ? 1 : b < 152 * 16 ? b : 152 * 16);
     gather_trees_kernel<<<blocks, 256, 0, s>>>(u, v, w, off, n_trees, total, list, coff, n_list,
                                                packed_total, cu, cv, cw);
 }
@@ -593,7 +617,8 @@ void launch_scatter_trees(const i32 *cep, const i32 *cvp, const i64 *off, i64 n_
 {
     if (n_list <= 0)
         return;
-    const unsigned blocks = (unsigned)(n_list < 152 * 16 ? n_list : 152 * 16);
+    const i64 b = (packed_total + n_list + 255) / 256;
+    const unsigned blocks = (unsigned)(b < 1 ? 1 : b < 152 * 16 ? b : 152 * 16);
     scatter_trees_kernel<<<blocks, 256, 0, s>>>(cep, cvp, off, n_trees, total, list, coff, n_list,
                                                 packed_total, ep, vp);
 }
