@@ -202,17 +202,26 @@ def log_uniform_sizes(rng, count: int, lo: int, hi: int) -> np.ndarray:
     return np.clip(np.rint(x).astype(np.int64), lo, hi)
 
 
+def batch_sizes(n_trees: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """The vertex counts `batch` draws for these arguments (without building
+    the trees), e.g. to shard a batch before generating it."""
+    return log_uniform_sizes(np.random.default_rng(seed), n_trees, lo, hi)
+
+
 def batch(n_trees: int, lo: int, hi: int, seed: int, families=("rrt", "path_skewed"),
-          sizes: Optional[np.ndarray] = None) -> Batch:
-    """Trees of log-uniform vertex counts in [lo, hi], family by a fair coin."""
+          sizes: Optional[np.ndarray] = None, only: Optional[np.ndarray] = None) -> Batch:
+    """Trees of log-uniform vertex counts in [lo, hi], family by a fair coin.
+    With `only`, just those trees of the same batch are built, in that order
+    (every tree has its own seed, so a subset equals the full batch's trees)."""
     rng = np.random.default_rng(seed)
     if sizes is None:
         sizes = log_uniform_sizes(rng, n_trees, lo, hi)
     fam_idx = rng.integers(0, len(families), size=n_trees)
     seeds = rng.integers(0, 2**62, size=n_trees)
+    picked = range(n_trees) if only is None else [int(t) for t in only]
     us, vs, ws, fams = [], [], [], []
-    offsets = np.zeros(n_trees + 1, np.int64)
-    for t in range(n_trees):
+    offsets = np.zeros(len(picked) + 1, np.int64)
+    for j, t in enumerate(picked):
         fam = families[int(fam_idx[t])]
         n = int(sizes[t])
         tr = rrt(n, int(seeds[t])) if fam == "rrt" else path_skewed(n, int(seeds[t]))
@@ -220,7 +229,7 @@ def batch(n_trees: int, lo: int, hi: int, seed: int, families=("rrt", "path_skew
         vs.append(tr.v)
         ws.append(tr.w)
         fams.append(fam)
-        offsets[t + 1] = offsets[t] + tr.m
+        offsets[j + 1] = offsets[j] + tr.m
     cat = (lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt))
     return Batch(cat(us, np.int32), cat(vs, np.int32), cat(ws, np.float32), offsets, fams)
 
