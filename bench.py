@@ -44,6 +44,9 @@ WORKLOADS = {
     "serving": dict(family="serving", n=2000, seed=5,
                     desc="Poisson arrivals of random recursive trees, vertex counts "
                          "log-uniform in [1e3, 1e7], uniform fp32 weights"),
+    "hdbscan_4m": dict(family="hdbscan", n=4_000_000, seed=3,
+                       desc="mutual-reachability spanning tree (minPts 16) of 4e6 3-D points "
+                            "from a 32-component Gaussian mixture"),
     "batched_4096": dict(family="batch", n=4096, seed=4,
                          desc="4096 trees, vertex counts log-uniform in [1e2, 1e6], "
                               "random recursive or skewed path by a fair coin"),
@@ -61,6 +64,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true", help="skip the path family line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check", action="store_true",
+                    help="compare the outputs with the oracle after the timed region")
     ap.add_argument("--async-api", action="store_true",
                     help="time pandora_dendrogram_async (worst-case level count, no host sync)")
     return ap.parse_args()
@@ -72,6 +77,8 @@ def make_tree(spec, n=None):
     n = n or spec["n"]
     if spec["family"] == "rrt":
         return inputs.rrt(n, spec["seed"])
+    if spec["family"] == "hdbscan":
+        return inputs.hdbscan_tree(n, spec["seed"])
     return inputs.path_skewed(n, spec["seed"])
 
 
@@ -238,7 +245,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": config_of(args, spec),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -733,13 +740,21 @@ def main():
         import oracle
         oracle.build()
         n_s = min(args.n or spec["n"], 10_000_000)
-        ts = make_tree(spec, n_s)
+        ts = t if n_s == (args.n or spec["n"]) else make_tree(spec, n_s)
         t0 = time.perf_counter()
         oracle.dendrogram(ts.u, ts.v, ts.w)
         sec = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": ts.m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{spec['family']} n={n_s} seed={spec['seed']}, "
                                           f"one thread, {sec:.1f} s"}
+    if args.check and rank == 0:
+        import oracle
+        oracle.build()
+        gep, gvp = pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
+        line["parity"] = {"oracle": "kruskal",
+                          "edge_parent_equal": bool(np.array_equal(gep.cpu().numpy(), oep)),
+                          "vertex_parent_equal": bool(np.array_equal(gvp.cpu().numpy(), ovp))}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
