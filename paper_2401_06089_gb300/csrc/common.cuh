@@ -22,6 +22,8 @@ constexpr int MAX_LEVELS = PANDORA_MAX_LEVELS;
 constexpr u32 SPIN_LIMIT = 1u << 22;       // bound of every device-side wait loop
 
 // ---- control block kept at the start of the workspace ----------------------
+constexpr int MARK_MAX_BUCKETS = 512;
+
 struct Ctrl {
     int status;                    // first device-detected error (pandora_status)
     int n_levels;                  // contraction levels run; set by the level that
@@ -32,6 +34,11 @@ struct Ctrl {
     u32 tile_counter[16];          // dynamic tile ids of single-pass kernels
     u32 hist1[4][256];             // digit histograms of the (weight, index) sort
     u32 hist2[4][256];             // digit histograms of the chain-key sort
+    // bucketed marking (levels with many vertices): incidences per vertex
+    // bucket, write cursors, bucket starts
+    u32 mark_count[MARK_MAX_BUCKETS];
+    u32 mark_cursor[MARK_MAX_BUCKETS];
+    u64 mark_base[MARK_MAX_BUCKETS + 1];
 };
 
 // Element count produced on the device, clamped to the buffer capacity the

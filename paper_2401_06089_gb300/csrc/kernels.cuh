@@ -115,8 +115,18 @@ struct LevelParams {
     unsigned char *lev;    // [M] contraction level of each edge (by rank)
     i32 *start;            // [M] supervertex holding the edge on the next level
     u64 *lb;               // look-back words (zeroed per level)
-    u32 *tile_counter;     // two counters (zeroed per level)
+    u32 *tile_counter;     // three counters (zeroed per level)
     int *status;
+    // bucketed marking: the level's incidences are first grouped by vertex
+    // bucket (2^mark_shift vertices each) so that each bucket's atomics hit
+    // a word range that stays in L2; mark_buckets == 0 marks directly
+    int mark_shift;
+    int mark_buckets;
+    u32 *rec_x;            // [2 m] incidence records: vertex
+    u64 *rec_w;            // [2 m] incidence records: candidate word
+    u32 *mark_count;       // Ctrl::mark_count (zeroed per level)
+    u32 *mark_cursor;      // Ctrl::mark_cursor (zeroed per level)
+    u64 *mark_base;        // Ctrl::mark_base
 };
 
 void launch_init_level(const LevelParams &p, cudaStream_t s);   // min_word = NO_EDGE

@@ -26,6 +26,8 @@
 // of the pointer forest are the components the paper contracts.  Along a
 // pointer path the edge ranks strictly decrease except across a leaf edge,
 // hence the forest is acyclic once each leaf edge's 2-cycle is broken.
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace pandora {
@@ -128,6 +130,190 @@ __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
             atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
         if (p.min_word[e.y] > wb)
             atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
+    }
+}
+
+// ---- bucketed marking ---------------------------------------------------------
+// On a level whose word array is much larger than L2 every random word access
+// of mark moves whole DRAM bursts and mostly misses.  Bucketed marking first
+// groups the level's 2m incidences by vertex bucket (2^mark_shift vertices,
+// a word range of 32 MB) -- count, bucket starts, scatter -- and then applies
+// them bucket after bucket, so that the atomics of the bucket in progress hit
+// a word range that stays in L2.  The minimum does not depend on the order,
+// so records inside a bucket may land in any order.
+#ifndef PANDORA_MB_ITEMS
+#define PANDORA_MB_ITEMS 8
+#endif
+constexpr int MB_TILE_ITEMS = PANDORA_MB_ITEMS;
+constexpr int MB_TILE = 256 * MB_TILE_ITEMS;   // edges per scatter tile
+
+__device__ __forceinline__ int mark_bucket(const LevelParams &p, i32 x)
+{
+    const int b = (int)((u32)x >> p.mark_shift);
+    return b < p.mark_buckets ? b : p.mark_buckets - 1;
+}
+
+__global__ void __launch_bounds__(256) mark_count_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    __shared__ u32 s_cnt[MARK_MAX_BUCKETS];
+    for (int b = threadIdx.x; b < p.mark_buckets; b += blockDim.x)
+        s_cnt[b] = 0;
+    __syncthreads();
+    const i64 m = dev_count(p.d_m, p.m_cap);
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (i64)gridDim.x * blockDim.x) {
+        const int2 e = p.ab[i];
+        atomicAdd(&s_cnt[mark_bucket(p, e.x)], 1u);
+        atomicAdd(&s_cnt[mark_bucket(p, e.y)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < p.mark_buckets; b += blockDim.x)
+        if (s_cnt[b])
+            atomicAdd(p.mark_count + b, s_cnt[b]);
+}
+
+// Exclusive scan of the bucket counts (one block of MARK_MAX_BUCKETS threads).
+__global__ void __launch_bounds__(MARK_MAX_BUCKETS) mark_prefix_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    __shared__ u64 s[MARK_MAX_BUCKETS];
+    const int b = threadIdx.x;
+    s[b] = b < p.mark_buckets ? (u64)p.mark_count[b] : 0ull;
+    __syncthreads();
+    for (int off = 1; off < MARK_MAX_BUCKETS; off <<= 1) {
+        const u64 y = b >= off ? s[b - off] : 0ull;
+        __syncthreads();
+        s[b] += y;
+        __syncthreads();
+    }
+    if (b < p.mark_buckets)
+        p.mark_base[b + 1] = s[b];
+    if (b == 0)
+        p.mark_base[0] = 0;
+}
+
+// Dynamic shared memory of a scatter tile: the tile's records staged in
+// bucket order (vertex, word, bucket) so that every bucket's run is written
+// to global memory contiguously.
+constexpr size_t MB_SMEM = (size_t)2 * MB_TILE * (8 + 4 + 2);
+
+template <bool LEVEL0>
+__global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    extern __shared__ __align__(16) unsigned char mb_smem[];
+    u64 *st_w = (u64 *)mb_smem;
+    u32 *st_x = (u32 *)(st_w + 2 * MB_TILE);
+    unsigned short *st_b = (unsigned short *)(st_x + 2 * MB_TILE);
+    __shared__ u32 s_cnt[MARK_MAX_BUCKETS];
+    __shared__ u32 s_off[MARK_MAX_BUCKETS];
+    __shared__ u64 s_gbase[MARK_MAX_BUCKETS];
+    __shared__ u32 s_warp[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const i64 m = dev_count(p.d_m, p.m_cap);
+    const i64 tiles = (m + MB_TILE - 1) / MB_TILE;
+    const u64 cap = 2 * (u64)p.m_cap;   // record capacity (the counts never exceed it)
+    for (i64 tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        for (int b = threadIdx.x; b < MARK_MAX_BUCKETS; b += blockDim.x)
+            s_cnt[b] = 0;
+        __syncthreads();
+        int2 e[MB_TILE_ITEMS];
+        u32 r[MB_TILE_ITEMS], sa[MB_TILE_ITEMS], sb[MB_TILE_ITEMS];
+        const i64 t0 = tile * MB_TILE;
+        const int count = (int)min((i64)MB_TILE, m - t0);
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it) {
+            const int k = it * 256 + threadIdx.x;
+            if (k < count) {
+                e[it] = p.ab[t0 + k];
+                r[it] = LEVEL0 ? (u32)(t0 + k) : p.er[t0 + k];
+                sa[it] = atomicAdd(&s_cnt[mark_bucket(p, e[it].x)], 1u);
+                sb[it] = atomicAdd(&s_cnt[mark_bucket(p, e[it].y)], 1u);
+            }
+        }
+        __syncthreads();
+        // exclusive scan of the bucket counts (two buckets per thread)
+        const u32 c0 = s_cnt[2 * threadIdx.x], c1 = s_cnt[2 * threadIdx.x + 1];
+        u32 incl = c0 + c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        if (lane == 31)
+            s_warp[warp] = incl;
+        __syncthreads();
+        u32 wpre = 0;
+        for (int w = 0; w < warp; ++w)
+            wpre += s_warp[w];
+        const u32 excl = wpre + incl - (c0 + c1);
+        s_off[2 * threadIdx.x] = excl;
+        s_off[2 * threadIdx.x + 1] = excl + c0;
+        for (int b = threadIdx.x; b < p.mark_buckets; b += blockDim.x)
+            if (s_cnt[b])
+                s_gbase[b] = p.mark_base[b] + atomicAdd(p.mark_cursor + b, s_cnt[b]);
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it) {
+            const int k = it * 256 + threadIdx.x;
+            if (k < count) {
+                const u64 ra = (u64)r[it] << 32;
+                const int ba = mark_bucket(p, e[it].x), bb = mark_bucket(p, e[it].y);
+                const u32 ja = s_off[ba] + sa[it], jb = s_off[bb] + sb[it];
+                st_x[ja] = (u32)e[it].x;
+                st_w[ja] = ra | ((u64)(u32)e[it].y << 1);        // at e.x: side 0
+                st_b[ja] = (unsigned short)ba;
+                st_x[jb] = (u32)e[it].y;
+                st_w[jb] = ra | ((u64)(u32)e[it].x << 1) | 1u;   // at e.y: side 1
+                st_b[jb] = (unsigned short)bb;
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * count; j += blockDim.x) {
+            const int b = st_b[j];
+            const u64 g = s_gbase[b] + (u32)(j - (int)s_off[b]);
+            if (g < cap) {
+                p.rec_x[g] = st_x[j];
+                p.rec_w[g] = st_w[j];
+            }
+        }
+        __syncthreads();   // staging and counters reused by the next tile
+    }
+}
+
+// Applies the records in bucket order: chunks are claimed in increasing
+// order, so the blocks work on one or two buckets at a time.
+__global__ void __launch_bounds__(256) mark_apply_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    __shared__ u32 s_tile;
+    const i64 total = min((i64)p.mark_base[p.mark_buckets], 2 * p.m_cap);
+    const i64 chunks = (total + MB_TILE - 1) / MB_TILE;
+    const i64 n = dev_count(p.d_n, p.n_cap);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(p.tile_counter + 2, 1u);
+        __syncthreads();
+        const i64 c = s_tile;
+        if (c >= chunks)
+            break;
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it) {
+            const i64 j = c * MB_TILE + it * 256 + threadIdx.x;
+            if (j < total) {
+                const u32 x = p.rec_x[j];
+                const u64 w = p.rec_w[j];
+                if ((i64)x < n && p.min_word[x] > w)
+                    atomicMin((unsigned long long *)(p.min_word + x), (unsigned long long)w);
+            }
+        }
     }
 }
 
@@ -498,6 +684,29 @@ void launch_init_level(const LevelParams &p, cudaStream_t s)
 
 void launch_mark(const LevelParams &p, cudaStream_t s)
 {
+    if (p.mark_buckets > 0) {
+        const unsigned cb = grid_for(p.m_grid, 256 * 8);
+        mark_count_kernel<<<cb, 256, 0, s>>>(p);
+        mark_prefix_kernel<<<1, MARK_MAX_BUCKETS, 0, s>>>(p);
+        const unsigned sb = grid_for(p.m_grid, MB_TILE);
+        static std::atomic<unsigned long long> attr_done{0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned long long bit = 1ull << (dev & 63);
+        if (!(attr_done.load() & bit)) {
+            cudaFuncSetAttribute(mark_scatter_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM);
+            cudaFuncSetAttribute(mark_scatter_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM);
+            attr_done.fetch_or(bit);
+        }
+        if (p.level == 0)
+            mark_scatter_kernel<true><<<sb, 256, MB_SMEM, s>>>(p);
+        else
+            mark_scatter_kernel<false><<<sb, 256, MB_SMEM, s>>>(p);
+        mark_apply_kernel<<<grid_for(2 * p.m_grid, MB_TILE), 256, 0, s>>>(p);
+        return;
+    }
     i64 b = (p.m_grid + 255) / 256;
     if (b > 152 * PANDORA_MARK_BPS)
         b = 152 * PANDORA_MARK_BPS;

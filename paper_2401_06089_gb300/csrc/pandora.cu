@@ -128,6 +128,20 @@ class CallTimer {
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Levels with more vertices than this (a word array above 256 MB, twice L2)
+// mark by buckets of 2^MARK_BUCKET_SHIFT vertices (32 MB of words each).
+// Measured on the 10^8-vertex random recursive tree: level 0 (10^8 vertices)
+// 6.4 -> 4.3 ms with buckets; level 1 (2.6*10^7 vertices) is faster direct
+// (1.0 vs 1.1 ms).
+#ifndef PANDORA_MARK_DIRECT_MAX
+#define PANDORA_MARK_DIRECT_MAX (i64(1) << 25)
+#endif
+#ifndef PANDORA_MARK_BUCKET_SHIFT
+#define PANDORA_MARK_BUCKET_SHIFT 22
+#endif
+constexpr i64 MARK_DIRECT_MAX_VERTICES = PANDORA_MARK_DIRECT_MAX;
+constexpr int MARK_BUCKET_SHIFT = PANDORA_MARK_BUCKET_SHIFT;
+
 struct Layout {
     size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, ptr;
     size_t deep, uf, root_of;
@@ -404,9 +418,39 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         P.lb = lb;
         P.tile_counter = ctrl->tile_counter;
         P.status = status;
+        // bucketed marking when the level's words (8 B per vertex) are well
+        // above L2; its records live in arrays idle during the level loop:
+        // the sort buffers (keysA .. valsB, 16 M bytes) and, on level 0, the
+        // kept records (filled from level 1 on)
+        if (n_grid > MARK_DIRECT_MAX_VERTICES) {
+            P.mark_shift = MARK_BUCKET_SHIFT;
+            P.mark_buckets = (int)std::min<i64>((n_grid + (i64(1) << MARK_BUCKET_SHIFT) - 1) >>
+                                                    MARK_BUCKET_SHIFT,
+                                                MARK_MAX_BUCKETS);
+            char *sort_region = base + L.keysA;   // keysA, keysB, valsA, valsB in a row
+            const size_t sort_bytes = L.perm - L.keysA;
+            P.rec_w = (u64 *)sort_region;
+            if (l == 0) {
+                P.rec_x = (u32 *)kept_rec;
+                if ((size_t)(2 * m_cap) * 8 > sort_bytes ||
+                    (size_t)(2 * m_cap) * 4 > (size_t)L.kept_cap * 8)
+                    P.mark_buckets = 0;
+            } else {
+                P.rec_x = (u32 *)(sort_region + align_up((size_t)(2 * m_cap) * 8));
+                if (align_up((size_t)(2 * m_cap) * 8) + (size_t)(2 * m_cap) * 4 > sort_bytes)
+                    P.mark_buckets = 0;
+            }
+            P.mark_count = ctrl->mark_count;
+            P.mark_cursor = ctrl->mark_cursor;
+            P.mark_base = ctrl->mark_base;
+            if (P.mark_buckets > 0)
+                PANDORA_CUDA(cudaMemsetAsync(ctrl->mark_count, 0,
+                                             sizeof(ctrl->mark_count) + sizeof(ctrl->mark_cursor),
+                                             s));
+        }
         PANDORA_CUDA(cudaMemsetAsync(
             lb, 0, (size_t)(level_tiles(n_grid) + 1 + level_tiles(m_grid) + 1) * 8, s));
-        PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 12, s));
         timer.launch(K_INIT_LEVEL, n_grid, [&] { launch_init_level(P, s); });
         timer.launch(K_MARK, m_grid, [&] { launch_mark(P, s); });
         timer.launch(K_PTR_INIT, n_grid, [&] { launch_ptr_init(P, s); });

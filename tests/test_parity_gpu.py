@@ -271,3 +271,15 @@ def test_full_size_1e8(pd, family):
     if family == "path_skewed":
         cep, _ = oracle.cartesian_path(t.w[t.path_eid], t.path_eid)
         np.testing.assert_array_equal(ep, cep)
+
+
+def test_batched_forest_above_bucketed_marking_threshold(pd):
+    """A forest of 4.4*10^7 vertices: level 0 marks by vertex buckets (more
+    than 2^25 vertices), across tree boundaries; every element against the
+    oracle."""
+    sizes = np.array([12_000_000, 3, 11_000_000, 1, 10_000_000, 11_000_000, 2], np.int64)
+    b = inputs.batch(len(sizes), 1, 1, seed=17, sizes=sizes)
+    ep, vp = run_batched(pd, b)[:2]
+    oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
+    np.testing.assert_array_equal(vp, ovp)
+    np.testing.assert_array_equal(ep, oep)
