@@ -443,7 +443,7 @@ def run_batched(args):
         "per_tree_async_ms": per_tree_async_ms,
         "speedup_vs_per_tree_blocking": per_tree_blocking_ms / ms,
         "speedup_vs_per_tree_async": per_tree_async_ms / ms,
-        "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
+        "gpu_launches_per_step": sum(e["kernels"] for e in prof.values()) / args.steps,
         "blocking_kernel_ms": blocking_ms,
         "blocking_dispatch_ms": dispatch_ms,
         "forest_async_graph_ms": forest_graph_ms,
@@ -610,7 +610,7 @@ def main():
     if args.async_api:
         # the asynchronous path only counts launches; time the kernels on
         # blocking calls of the same tree right after the timed region
-        launches_async = sum(e["launches"] for e in prof.values())
+        launches_async = sum(e["kernels"] for e in prof.values())
         pd.profile_start(timing=True)
         for _ in range(args.steps):
             pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
@@ -619,7 +619,7 @@ def main():
         for e in prof.values():
             e["launches_async"] = None
         timing_note = ("kernel split from blocking calls after the timed region; "
-                       f"{launches_async} launches in the timed region")
+                       f"{launches_async} kernel launches in the timed region")
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     if dist:
@@ -671,8 +671,8 @@ def main():
         "roofline": roofline,
         "path_model_gbs": path_roofline,
         "path_model_frac": path_roofline / peak,
-        "gpu_launches": sum(e["launches"] for e in prof.values()),
-        "gpu_launches_per_step": sum(e["launches"] for e in prof.values()) / args.steps,
+        "gpu_launches": sum(e["kernels"] for e in prof.values()),
+        "gpu_launches_per_step": sum(e["kernels"] for e in prof.values()) / args.steps,
         "kernels": kernels,
         "kernel_timing": timing_note,
         "api": "pandora_dendrogram_async" if args.async_api else "pandora_dendrogram",

@@ -268,6 +268,9 @@ typedef struct pandora_profile {
     int64_t launches[PANDORA_PROFILE_SLOTS];
     int64_t elements[PANDORA_PROFILE_SLOTS];      /* items processed (edges or vertices) */
     double total_ms[PANDORA_PROFILE_SLOTS];
+    int64_t kernels[PANDORA_PROFILE_SLOTS];       /* CUDA kernels launched (a step of the
+                                                     path can take several: the bucketed
+                                                     marking 4, root finding 4) */
 } pandora_profile;
 
 int pandora_profile_start(int with_timing);

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("n_kernels", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("name", (ctypes.c_char * 32) * 16), ("launches", ctypes.c_int64 * 16),
-                ("elements", ctypes.c_int64 * 16), ("total_ms", ctypes.c_double * 16)]
+                ("elements", ctypes.c_int64 * 16), ("total_ms", ctypes.c_double * 16),
+                ("kernels", ctypes.c_int64 * 16)]
 
 
 class Tuning(ctypes.Structure):
@@ -185,13 +186,16 @@ def profile_start(timing: bool = False) -> None:
 
 
 def profile_read() -> dict:
-    """{kernel: {"launches", "elements", "ms"}} since the last profile_start."""
+    """{step: {"launches", "kernels", "elements", "ms"}} since the last
+    profile_start ("launches" counts steps of the path, "kernels" the CUDA
+    kernels they launched)."""
     pr = Profile()
     load_library().pandora_profile_read(ctypes.byref(pr))
     out = {}
     for k in range(pr.n_kernels):
         name = pr.name[k].value.decode()
-        out[name] = {"launches": int(pr.launches[k]), "elements": int(pr.elements[k]),
+        out[name] = {"launches": int(pr.launches[k]), "kernels": int(pr.kernels[k]),
+                     "elements": int(pr.elements[k]),
                      "ms": float(pr.total_ms[k]) if pr.timing else None}
     return out
 

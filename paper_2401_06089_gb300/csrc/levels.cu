@@ -145,6 +145,9 @@ __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
 #define PANDORA_MB_ITEMS 8
 #endif
 constexpr int MB_TILE_ITEMS = PANDORA_MB_ITEMS;
+#ifndef PANDORA_MARK_APPLY_BPS
+#define PANDORA_MARK_APPLY_BPS 4
+#endif
 constexpr int MB_TILE = 256 * MB_TILE_ITEMS;   // edges per scatter tile
 
 __device__ __forceinline__ int mark_bucket(const LevelParams &p, i32 x)
@@ -704,7 +707,10 @@ void launch_mark(const LevelParams &p, cudaStream_t s)
             mark_scatter_kernel<true><<<sb, 256, MB_SMEM, s>>>(p);
         else
             mark_scatter_kernel<false><<<sb, 256, MB_SMEM, s>>>(p);
-        mark_apply_kernel<<<grid_for(2 * p.m_grid, MB_TILE), 256, 0, s>>>(p);
+        i64 ab = (2 * p.m_grid + MB_TILE - 1) / MB_TILE;
+        if (ab > 152 * PANDORA_MARK_APPLY_BPS)
+            ab = 152 * PANDORA_MARK_APPLY_BPS;
+        mark_apply_kernel<<<(unsigned)(ab < 1 ? 1 : ab), 256, 0, s>>>(p);
         return;
     }
     i64 b = (p.m_grid + 255) / 256;

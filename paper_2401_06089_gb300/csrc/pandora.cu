@@ -35,6 +35,7 @@ struct Profiler {
     std::mutex mu;
     bool timing = false;
     i64 launches[K_SLOTS] = {};
+    i64 kernels[K_SLOTS] = {};
     i64 elements[K_SLOTS] = {};
     double ms[K_SLOTS] = {};
     std::vector<cudaEvent_t> free_events;
@@ -60,7 +61,10 @@ class CallTimer {
     }
     ~CallTimer() { flush(); }
 
-    template <class F> void launch(int slot, i64 elements, F &&f)
+    template <class F> void launch(int slot, i64 elements, F &&f) { launch(slot, elements, 1, f); }
+
+    // `kernels`: CUDA kernels the step launches
+    template <class F> void launch(int slot, i64 elements, int kernels, F &&f)
     {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timing_) {
@@ -72,13 +76,14 @@ class CallTimer {
         f();
         if (timing_ && b)
             cudaEventRecord(b, s_);
-        recs_.push_back({slot, elements, a, b});
+        recs_.push_back({slot, elements, kernels, a, b});
     }
 
   private:
     struct Rec {
         int slot;
         i64 elements;
+        int kernels;
         cudaEvent_t a, b;
     };
     cudaEvent_t get()
@@ -107,6 +112,7 @@ class CallTimer {
         std::lock_guard<std::mutex> lock(p.mu);
         for (const Rec &r : recs_) {
             p.launches[r.slot] += 1;
+            p.kernels[r.slot] += r.kernels;
             p.elements[r.slot] += r.elements;
             if (r.a && r.b) {
                 float ms = 0.f;
@@ -452,9 +458,9 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
             lb, 0, (size_t)(level_tiles(n_grid) + 1 + level_tiles(m_grid) + 1) * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 12, s));
         timer.launch(K_INIT_LEVEL, n_grid, [&] { launch_init_level(P, s); });
-        timer.launch(K_MARK, m_grid, [&] { launch_mark(P, s); });
+        timer.launch(K_MARK, m_grid, P.mark_buckets > 0 ? 4 : 1, [&] { launch_mark(P, s); });
         timer.launch(K_PTR_INIT, n_grid, [&] { launch_ptr_init(P, s); });
-        timer.launch(K_COMPRESS, n_grid, [&] { launch_compress(P, s); });
+        timer.launch(K_COMPRESS, n_grid, 4, [&] { launch_compress(P, s); });
         timer.launch(K_COMPACT, m_grid, [&] { launch_compact(P, s); });
         PANDORA_CUDA(cudaGetLastError());
         n_levels = l + 1;
@@ -933,6 +939,7 @@ int pandora_profile_start(int with_timing)
     p.timing = with_timing != 0;
     for (int k = 0; k < K_SLOTS; ++k) {
         p.launches[k] = 0;
+        p.kernels[k] = 0;
         p.elements[k] = 0;
         p.ms[k] = 0.0;
     }
@@ -951,6 +958,7 @@ int pandora_profile_read(pandora_profile *out)
     for (int k = 0; k < K_SLOTS; ++k) {
         std::strncpy(out->name[k], kSlotNames[k], sizeof(out->name[k]) - 1);
         out->launches[k] = p.launches[k];
+        out->kernels[k] = p.kernels[k];
         out->elements[k] = p.elements[k];
         out->total_ms[k] = p.timing ? p.ms[k] : -1.0;
     }
