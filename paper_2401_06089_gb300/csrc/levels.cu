@@ -404,8 +404,9 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
 //    appended to the deep list.
 // 2. Only when the deep list is not empty (long monotone chains, e.g. a path
 //    whose weights increase along it), union-find over the deep vertices:
-//    uf_union hooks the larger representative under the smaller one (CAS,
-//    path halving) for every deep vertex and its deep pointer target; the top
+//    uf_union hooks the representative of lower hashed priority under the
+//    other (CAS, path halving) for every deep vertex and its deep pointer
+//    target; the top
 //    of each deep component (its pointer target is resolved) stores the dense
 //    root id at the component's representative (uf_tops), and uf_finish hands
 //    it to every member.  This is the union-find contraction the paper uses
@@ -494,6 +495,24 @@ __device__ __forceinline__ i32 uf_find(i32 *uf, i32 a, int *status, i64 bound)
     }
 }
 
+// Linking priority of a union-find representative: the lowbias32 integer
+// hash (C. Wellons), a bijection of 32-bit words, so priorities are distinct.
+// Hooking by a pseudo-random priority instead of by id keeps the union-find
+// trees shallow whatever the labelling: with ids, a path labelled in order
+// whose weights increase along it would hook every vertex under its
+// neighbour at once, one chain as long as the path, which every later find
+// would walk.
+__device__ __forceinline__ u32 uf_priority(i32 a)
+{
+    u32 x = (u32)a;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 __device__ __forceinline__ i64 deep_count(const LevelParams &p)
 {
     return dev_count(p.d_n_deep, p.n_cap);
@@ -511,14 +530,15 @@ __global__ void __launch_bounds__(256) uf_union_kernel(const LevelParams p)
         const i32 y = ld_volatile(p.ptr + x);
         if (ld_volatile(p.ptr + y) < 0)
             continue;   // y is resolved: x tops its deep component
-        // both deep: hook the larger representative under the smaller
+        // both deep: hook the representative of lower priority under the
+        // other one (see uf_priority)
         i32 a = x, b = y;
         for (i64 iter = 0;; ++iter) {
             a = uf_find(p.uf, a, p.status, bound);
             b = uf_find(p.uf, b, p.status, bound);
             if (a == b)
                 break;
-            if (a < b) {
+            if (uf_priority(a) > uf_priority(b)) {
                 const i32 t = a;
                 a = b;
                 b = t;

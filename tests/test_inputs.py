@@ -46,3 +46,18 @@ def test_hdbscan_tree_is_a_spanning_tree(n):
     assert t.m == n - 1
     ep, vp = oracle.dendrogram(t.u, t.v, t.w)   # raises unless it is a tree
     assert (ep == -1).sum() == 1
+
+
+def test_increasing_path_construction_against_oracle():
+    """The generator of the maximum-size test, at a small size on the CPU: its
+    closed form holds for the oracle's dendrogram."""
+    torch = pytest.importorskip("torch")
+    import importlib.util, os
+    spec = importlib.util.spec_from_file_location(
+        "tpg", os.path.join(os.path.dirname(__file__), "test_parity_gpu.py"))
+    tpg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(tpg)
+    for m in (1, 2, 7, 1000, 65_537):
+        u, v, w, pos = tpg.strictly_increasing_path(m, "cpu", a_mul=1_000_003)
+        ep, vp = oracle.dendrogram(u.numpy(), v.numpy(), w.numpy())
+        tpg.check_increasing_path(torch.from_numpy(ep), torch.from_numpy(vp), pos)

@@ -251,3 +251,4 @@ def test_contraction_level_invariants(gen):
         assert lv["n"] == ml + 1
         assert lv["n_next"] == n_alpha + 1
     assert not levels[-1]["alpha"].any()
+

@@ -283,3 +283,94 @@ def test_batched_forest_above_bucketed_marking_threshold(pd):
     oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
     np.testing.assert_array_equal(vp, ovp)
     np.testing.assert_array_equal(ep, oep)
+
+
+def strictly_increasing_path(m, device, a_mul=1_000_000_007, b_add=12345):
+    """A path of m edges whose weights strictly increase along it: path edge i
+    gets the fp32 whose order key (the sort's sign-flip transform) is
+    0x00800000 + i -- consecutive floats upward from -FLT_MAX, through
+    -0.0 < +0.0 and the subnormals (finite for m <= 2^31 - 2).  Caller position
+    c holds path edge (a_mul * c + b_add) mod m, an affine permutation, with a
+    hashed orientation.  Returns (u, v, w, pos), pos[i] = caller position of
+    path edge i; everything elementwise, so it runs on the device at any size."""
+    import math
+    assert math.gcd(a_mul, m) == 1
+    c = torch.arange(m, dtype=torch.int64, device=device)
+    order = (c * a_mul + b_add) % m
+    flip = ((c * 0x9E3779B1) >> 16) & 1
+    a = order.to(torch.int32)
+    u = torch.where(flip == 1, a + 1, a)
+    v = torch.where(flip == 1, a, a + 1)
+    del flip, a
+    k = order + 0x00800000
+    bits = torch.where(k >= 2**31, k - 2**31, 0xFFFFFFFF - k)
+    del k
+    bits = torch.where(bits >= 2**31, bits - 2**32, bits).to(torch.int32)
+    w = bits.view(torch.float32)
+    del bits, order
+    inv = pow(a_mul, -1, m)
+    i = c   # reuse: c now plays the path index
+    pos = (((i - b_add) % m) * inv % m).to(torch.int32)
+    del c, i
+    return u, v, w, pos
+
+
+def check_increasing_path(ep, vp, pos):
+    """Closed form of a path whose weights increase along it: path edge i hangs
+    from path edge i + 1, the last is the root; vertex x's lightest edge is
+    path edge x - 1 (edge 0 for vertex 0)."""
+    assert torch.equal(ep[pos[:-1].long()], pos[1:])
+    assert int(ep[pos[-1].long()]) == -1
+    assert int(vp[0]) == int(pos[0])
+    assert torch.equal(vp[1:], pos)
+
+
+def test_maximum_size_path(pd):
+    """The largest input the ABI takes: n_edges + 1 = INT32_MAX vertices
+    (2^31 - 2 edges, about 210 GB on the device with the workspace), a path
+    from `strictly_increasing_path` in shuffled order with random orientation;
+    every element is checked against the closed form.  Generated and checked on
+    the device to keep host memory small."""
+    import time
+    t_start = time.perf_counter()
+
+    def mark(what):
+        print(f"[max-size] {what}: {time.perf_counter() - t_start:.1f} s", flush=True)
+
+    free, total = torch.cuda.mem_get_info()
+    m = 2**31 - 2
+    if free < 240 * 2**30:
+        pytest.skip(f"needs about 240 GB free on the device ({free / 2**30:.0f} GB)")
+    dev = torch.device("cuda")
+    u, v, w, pos = strictly_increasing_path(m, dev)
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    mark("inputs built")
+    ws = torch.empty(pd.workspace_size(m), dtype=torch.uint8, device=dev)
+    ep = torch.empty(m, dtype=torch.int32, device=dev)
+    vp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    mark("dendrogram")
+    del ws, u, v, w
+    torch.cuda.empty_cache()
+    check_increasing_path(ep, vp, pos)
+    mark("checked")
+
+
+def test_path_in_order_increasing_weights(pd):
+    """The union-find worst case for id-ordered hooking: a path labelled and
+    listed in order with strictly increasing weights (every vertex's pointer
+    chain runs to one end), 3*10^7 vertices; checked against the closed form
+    (each edge hangs from the next one) and, on a prefix, the oracle."""
+    m = 30_000_000
+    u = np.arange(m, dtype=np.int32)
+    v = u + 1
+    w = np.arange(1, m + 1, dtype=np.uint32).view(np.float32)   # consecutive positive floats
+    ep, vp = run_gpu(pd, inputs.Tree(u, v, w))
+    np.testing.assert_array_equal(ep[:-1], np.arange(1, m, dtype=np.int32))
+    assert ep[-1] == -1
+    np.testing.assert_array_equal(vp[1:], np.arange(m, dtype=np.int32))
+    assert vp[0] == 0
+    t = inputs.Tree(u[:100_000], v[:100_000], w[:100_000])
+    assert_parity(pd, t)
