@@ -92,6 +92,24 @@ int pandora_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64
                        int32_t *edge_parent, int32_t *vertex_parent, void *stream);
 
 /*
+ * As pandora_dendrogram, but u, v, w, edge_parent and vertex_parent are HOST
+ * memory (pinned memory copies fastest; pageable memory works).  The paper has
+ * no counterpart: this is the transfer schedule around its method for data
+ * that lives on the host.  Device memory for the inputs, the outputs and the
+ * workspace comes from the library's pool.  The copies overlap the path: the
+ * weights go first (the histogram pass needs only them) while the endpoints
+ * follow on a second stream, which the first sort pass waits for;
+ * vertex_parent is copied back on a third stream as soon as level 0 has
+ * written it (Eq. 1), while the other levels, the expansion and the linking
+ * run; edge_parent follows the last kernel.  Blocking: returns when both
+ * outputs are in host memory (the stream is synchronised).  Host buffers must
+ * stay valid and unmodified until the call returns.  Errors as
+ * pandora_dendrogram.
+ */
+int pandora_dendrogram_host(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                            int32_t *edge_parent, int32_t *vertex_parent, void *stream);
+
+/*
  * Bytes of caller workspace that pandora_dendrogram_ws / _batched_ws need for
  * a total of `total_edges` edges in `n_trees` trees (n_trees = 1 for a single
  * tree).  Writes the size to *bytes.  Host only; enqueues nothing.

@@ -13,6 +13,7 @@ from ._binding import (  # noqa: F401
     dendrogram_batched,
     dendrogram_batched_async,
     dendrogram_batched_planned,
+    dendrogram_host,
     get_tuning,
     library_path,
     load_tuning,

@@ -83,6 +83,7 @@ def load_library():
         SZ = ctypes.c_size_t
         lib.pandora_dendrogram.argtypes = [P, P, P, I64, P, P, P]
         lib.pandora_dendrogram_ws.argtypes = [P, P, P, I64, P, P, P, SZ, P, P]
+        lib.pandora_dendrogram_host.argtypes = [P, P, P, I64, P, P, P]
         lib.pandora_dendrogram_batched.argtypes = [P, P, P, P, I64, I64, P, P, P]
         lib.pandora_dendrogram_batched_ws.argtypes = [P, P, P, P, I64, I64, P, P, P, SZ, P, P]
         lib.pandora_workspace_size.argtypes = [I64, I64, ctypes.POINTER(SZ)]
@@ -103,7 +104,7 @@ def load_library():
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
                      "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
-                     "pandora_dendrogram_batched_planned"):
+                     "pandora_dendrogram_batched_planned", "pandora_dendrogram_host"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     _apply_default_tuning()
@@ -270,6 +271,36 @@ def dendrogram(u, v, w, *, workspace=None, stats: bool = False, out=None):
         raise PandoraError(st, "pandora_dendrogram")
     if stats:
         return ep, vp, _stats_dict(st_out)
+    return ep, vp
+
+
+def dendrogram_host(u, v, w, *, out=None, device=None):
+    """``pandora_dendrogram_host``: CPU tensors in (pinned copies fastest),
+    CPU tensors out; the library moves the data and overlaps the copies with
+    the path.  ``device``: the CUDA device to run on (default: current)."""
+    torch = _torch()
+    lib = load_library()
+    m = w.numel()
+    for t, dt, name in ((u, torch.int32, "u"), (v, torch.int32, "v"), (w, torch.float32, "w")):
+        if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() != m:
+            raise ValueError(f"{name} must be a contiguous CPU {dt} tensor of {m} elements")
+    if out is None:
+        pin = u.is_pinned()
+        ep = torch.empty(m, dtype=torch.int32, pin_memory=pin)
+        vp = torch.empty(m + 1, dtype=torch.int32, pin_memory=pin)
+    else:
+        ep, vp = out
+        for t, n, name in ((ep, m, "edge_parent"), (vp, m + 1, "vertex_parent")):
+            if t.device.type != "cpu" or t.dtype != torch.int32 or not t.is_contiguous() \
+                    or t.numel() != n:
+                raise ValueError(f"{name} must be a contiguous CPU int32 tensor of {n} elements")
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_dendrogram_host(u.data_ptr(), v.data_ptr(), w.data_ptr(), m,
+                                         ep.data_ptr(), vp.data_ptr(), stream)
+    if st:
+        raise PandoraError(st, "pandora_dendrogram_host")
     return ep, vp
 
 

@@ -256,9 +256,34 @@ int level_bound(i64 M)
 //             so the call can be captured in a CUDA graph; kernels of levels
 //             past the last one exit at once.  The device status stays in the
 //             workspace (pandora_workspace_status).
+// Hooks of the host-buffer entry point: the stream waits for uv_ready (the
+// endpoints' host-to-device copy) only before the first sort pass, which is
+// the first step that reads them; vp_done is recorded once level 0 has
+// written vertex_parent, so its device-to-host copy overlaps the rest.
+struct Overlap {
+    cudaEvent_t uv_ready = nullptr;
+    cudaEvent_t vp_done = nullptr;
+    cudaStream_t vp_stream = nullptr;   // copies vertex_parent to vp_host after vp_done
+    i32 *vp_host = nullptr;
+};
+
+// Enqueues the copy of vertex_parent (N entries) to the host once it is final.
+int overlap_vp_copy(const Overlap *ov, const i32 *vp, i64 N, cudaStream_t s)
+{
+    if (!ov || !ov->vp_done)
+        return PANDORA_OK;
+    PANDORA_CUDA(cudaEventRecord(ov->vp_done, s));
+    if (ov->vp_stream && ov->vp_host) {
+        PANDORA_CUDA(cudaStreamWaitEvent(ov->vp_stream, ov->vp_done, 0));
+        PANDORA_CUDA(cudaMemcpyAsync(ov->vp_host, vp, (size_t)N * 4, cudaMemcpyDeviceToHost,
+                                     ov->vp_stream));
+    }
+    return PANDORA_OK;
+}
+
 int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64 *d_off,
              i32 *ep, i32 *vp, void *ws, size_t ws_bytes, pandora_stats *stats, cudaStream_t s,
-             bool blocking)
+             bool blocking, const Overlap *ov = nullptr)
 {
     const i64 N = M + T;
     if (stats)
@@ -298,6 +323,8 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         timer.launch(K_CHECK_OFFSETS, T + 1, [&] { launch_check_offsets(d_off, T, M, status, s); });
     if (M == 0) {
         timer.launch(K_FILL, N, [&] { launch_fill(vp, N, -1, s); });
+        if (int e = overlap_vp_copy(ov, vp, N, s))
+            return e;
         PANDORA_CUDA(cudaGetLastError());
         if (!blocking)
             return PANDORA_OK;
@@ -325,6 +352,9 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     // (2N entries) and ptr (N)
     // (pvA starts at a 256-byte boundary: the sort reads these arrays with
     // bulk copies, which need 16-byte aligned sources)
+    // the histogram pass read only the weights; the endpoints must be here now
+    if (ov && ov->uv_ready)
+        PANDORA_CUDA(cudaStreamWaitEvent(s, ov->uv_ready, 0));
     u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + ((L.kept_cap + 63) & ~(i64)63);
     u32 *puB = (u32 *)min_word, *pvB = (u32 *)ptr;
     const u32 *cur_k = nullptr, *cur_v = nullptr, *cur_u = nullptr, *cur_w = nullptr;
@@ -460,6 +490,9 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         timer.launch(K_INIT_LEVEL, n_grid, [&] { launch_init_level(P, s); });
         timer.launch(K_MARK, m_grid, P.mark_buckets > 0 ? 4 : 1, [&] { launch_mark(P, s); });
         timer.launch(K_PTR_INIT, n_grid, [&] { launch_ptr_init(P, s); });
+        if (l == 0)   // vertex_parent is final after level 0's ptr_init
+            if (int e = overlap_vp_copy(ov, vp, N, s))
+                return e;
         timer.launch(K_COMPRESS, n_grid, 4, [&] { launch_compress(P, s); });
         timer.launch(K_COMPACT, m_grid, [&] { launch_compact(P, s); });
         PANDORA_CUDA(cudaGetLastError());
@@ -856,6 +889,121 @@ int run_pooled(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i
     return st;
 }
 
+// Streams and events of the host-buffer entry point, one set per device and
+// host thread (created once, kept for the process).
+struct HostIoRes {
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_alloc = nullptr, ev_uv = nullptr, ev_vp = nullptr, ev_out = nullptr;
+};
+HostIoRes *host_io_res(int dev)
+{
+    static thread_local std::map<int, HostIoRes> res;
+    auto it = res.find(dev);
+    if (it != res.end())
+        return &it->second;
+    HostIoRes r;
+    if (cudaStreamCreateWithFlags(&r.s_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&r.s_out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.ev_alloc, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.ev_uv, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.ev_vp, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    return &(res[dev] = r);
+}
+
+// One tree from host buffers to host buffers.  Device memory (inputs,
+// outputs, workspace) comes from the library pool on `s`.  The weights go
+// first on `s` (the histogram pass needs only them), the endpoints in
+// parallel on a second stream that the first sort pass waits for;
+// vertex_parent goes back on a third stream as soon as level 0 has written
+// it, overlapping the other levels, the expansion and the linking;
+// edge_parent follows the last kernel.  Blocking.
+int run_host(const i32 *hu, const i32 *hv, const float *hw, i64 M, i32 *hep, i32 *hvp,
+             cudaStream_t s)
+{
+    int dev = 0;
+    PANDORA_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = library_pool(dev);
+    HostIoRes *r = host_io_res(dev);
+    if (!pool || !r)
+        return PANDORA_ERR_CUDA;
+    const i64 N = M + 1;
+    const size_t io_bytes = align_up((size_t)M * 4) * 4 + align_up((size_t)N * 4);
+    const size_t ws_bytes = total_workspace(M, 1);
+    char *io = nullptr;
+    void *ws = nullptr;
+    if (cudaMallocFromPoolAsync((void **)&io, io_bytes, pool, s) != cudaSuccess ||
+        cudaMallocFromPoolAsync(&ws, ws_bytes, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        if (io)
+            cudaFreeAsync(io, s);
+        return PANDORA_ERR_OUT_OF_MEMORY;
+    }
+    const size_t a = align_up((size_t)M * 4);
+    i32 *du = (i32 *)io, *dv = (i32 *)(io + a);
+    float *dw = (float *)(io + 2 * a);
+    i32 *dep = (i32 *)(io + 3 * a), *dvp = (i32 *)(io + 4 * a);
+    int st = PANDORA_OK;
+    do {
+        if (cudaEventRecord(r->ev_alloc, s) != cudaSuccess ||
+            cudaStreamWaitEvent(r->s_in, r->ev_alloc, 0) != cudaSuccess ||
+            cudaStreamWaitEvent(r->s_out, r->ev_alloc, 0) != cudaSuccess) {
+            st = PANDORA_ERR_CUDA;
+            break;
+        }
+        if (M > 0 &&
+            (cudaMemcpyAsync(dw, hw, (size_t)M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+             cudaMemcpyAsync(du, hu, (size_t)M * 4, cudaMemcpyHostToDevice, r->s_in) != cudaSuccess ||
+             cudaMemcpyAsync(dv, hv, (size_t)M * 4, cudaMemcpyHostToDevice, r->s_in) != cudaSuccess)) {
+            st = PANDORA_ERR_CUDA;
+            break;
+        }
+        if (cudaEventRecord(r->ev_uv, r->s_in) != cudaSuccess) {
+            st = PANDORA_ERR_CUDA;
+            break;
+        }
+        const pandora_tuning tn = tuning_snapshot();
+        const i64 cutoff = std::min<i64>(tn.small_max_edges, small_tree_capacity());
+        if (M >= 1 && M <= cutoff) {
+            // one small tree: the single-block solver, nothing to overlap
+            if (cudaStreamWaitEvent(s, r->ev_uv, 0) != cudaSuccess) {
+                st = PANDORA_ERR_CUDA;
+                break;
+            }
+            st = run(du, dv, dw, M, 1, nullptr, dep, dvp, ws, ws_bytes, nullptr, s, true);
+            if (st == PANDORA_OK &&
+                (cudaMemcpyAsync(hvp, dvp, (size_t)N * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                 cudaMemcpyAsync(hep, dep, (size_t)M * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess))
+                st = PANDORA_ERR_CUDA;
+            break;
+        }
+        Overlap ov;
+        ov.uv_ready = r->ev_uv;
+        ov.vp_done = r->ev_vp;
+        ov.vp_stream = r->s_out;
+        ov.vp_host = hvp;
+        st = run_core(du, dv, dw, M, 1, nullptr, dep, dvp, ws, ws_bytes, nullptr, s, true, &ov);
+        if (st != PANDORA_OK)
+            break;
+        if (M > 0 &&
+            cudaMemcpyAsync(hep, dep, (size_t)M * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            st = PANDORA_ERR_CUDA;
+            break;
+        }
+    } while (false);
+    // s waits for the other streams' last work before the memory goes back
+    cudaEventRecord(r->ev_out, r->s_out);
+    cudaStreamWaitEvent(s, r->ev_out, 0);
+    cudaEventRecord(r->ev_uv, r->s_in);
+    cudaStreamWaitEvent(s, r->ev_uv, 0);
+    cudaFreeAsync(ws, s);
+    cudaFreeAsync(io, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == PANDORA_OK)
+        st = PANDORA_ERR_CUDA;
+    return st;
+}
+
 }  // namespace
 
 // Entry for other translation units of the library (the allocation-free
@@ -890,6 +1038,14 @@ int pandora_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64
         return e;
     return run_pooled(u, v, w, n_edges, 1, nullptr, edge_parent, vertex_parent,
                       (cudaStream_t)stream);
+}
+
+int pandora_dendrogram_host(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                            int32_t *edge_parent, int32_t *vertex_parent, void *stream)
+{
+    if (int e = check_common(u, v, w, n_edges, 1, edge_parent, vertex_parent))
+        return e;
+    return run_host(u, v, w, n_edges, edge_parent, vertex_parent, (cudaStream_t)stream);
 }
 
 int pandora_dendrogram_ws(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
