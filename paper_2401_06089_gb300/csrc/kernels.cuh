@@ -47,6 +47,7 @@ struct OnesweepParams {
     i64 n;
     int shift;
     const u32 *hist;       // [256] digit counts of this pass
+    const u32 *bin_base;   // [256] their exclusive scan, or nullptr (scanned per tile)
     u64 *lb;               // [tiles * 256] look-back words, zeroed
     u32 *tile_counter;     // zeroed
     int *status;
@@ -64,6 +65,8 @@ __host__ __device__ inline i64 onesweep_tiles(i64 n) { return (n + OS_TILE - 1) 
 void launch_hist_weights(const float *w, i64 n, u32 *hist /*[4][256]*/, int *status,
                          cudaStream_t s);
 void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s);
+// base[r][d] = sum of hist[r][d'] over d' < d, for `rows` rows of 256
+void launch_hist_scan(const u32 *hist, u32 *base, int rows, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // levels.cu - one contraction level (Eq. 1, Eq. 2, Section 3.2)

@@ -334,7 +334,10 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     }
 
     // ---- 1. sort by (weight, index) -------------------------------------------
-    timer.launch(K_HIST_WEIGHTS, M, [&] { launch_hist_weights(w, M, &ctrl->hist1[0][0], status, s); });
+    timer.launch(K_HIST_WEIGHTS, M, 2, [&] {
+        launch_hist_weights(w, M, &ctrl->hist1[0][0], status, s);
+        launch_hist_scan(&ctrl->hist1[0][0], &ctrl->base1[0][0], 4, s);
+    });
     std::vector<int> passes = {0, 1, 2, 3};
     if (blocking) {
         static thread_local u32 hhist[4][RADIX];
@@ -365,6 +368,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         P.n = M;
         P.shift = 8 * passes[k];
         P.hist = ctrl->hist1[passes[k]];
+        P.bin_base = ctrl->base1[passes[k]];
         P.lb = lb;
         P.tile_counter = &ctrl->tile_counter[0];
         P.status = status;
@@ -541,7 +545,10 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     E.n_trees = T;
     E.hist = &ctrl->hist2[0][0];
     E.status = status;
-    timer.launch(K_EXPAND, M, [&] { launch_expand(E, table, s); });
+    timer.launch(K_EXPAND, M, 2, [&] {
+        launch_expand(E, table, s);
+        launch_hist_scan(&ctrl->hist2[0][0], &ctrl->base2[0][0], 4, s);
+    });
     PANDORA_CUDA(cudaGetLastError());
     const u64 max_key = (u64)root_base + (u64)T - 1;
     int bits = 0;
@@ -567,6 +574,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         P.n = M;
         P.shift = 8 * passes2[k];
         P.hist = ctrl->hist2[passes2[k]];
+        P.bin_base = ctrl->base2[passes2[k]];
         P.lb = lb;
         P.tile_counter = &ctrl->tile_counter[0];
         P.status = status;

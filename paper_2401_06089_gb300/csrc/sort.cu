@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(OS_THREADS, (FLAGS & OS_PAYLOAD_UV) ? OS_MIN_B
         }
     }
     // global start of every digit's bucket (exclusive scan of the pass histogram)
-    const u32 bin_base = digit_exclusive_scan(tid < RADIX ? p.hist[tid] : 0u, s_warp);
+    // global start of every digit's bucket: scanned once per pass when the
+    // caller provides it, else here
+    const u32 bin_base = p.bin_base ? (tid < RADIX ? p.bin_base[tid] : 0u)
+                                    : digit_exclusive_scan(tid < RADIX ? p.hist[tid] : 0u, s_warp);
     mbar_wait_bounded(&s_bar[0], 0, p.status);
     __syncthreads();   // plain-loaded tail elements visible to all
 
@@ -383,7 +386,20 @@ __global__ void __launch_bounds__(OS_THREADS, (FLAGS & OS_PAYLOAD_UV) ? OS_MIN_B
     }
 }
 
+// Exclusive scan of each 256-digit histogram row (one block per row).
+__global__ void __launch_bounds__(RADIX) hist_scan_kernel(const u32 *hist, u32 *base)
+{
+    __shared__ u32 s_warp[RADIX / 32];
+    const u32 x = hist[blockIdx.x * RADIX + threadIdx.x];
+    base[blockIdx.x * RADIX + threadIdx.x] = digit_exclusive_scan(x, s_warp);
+}
+
 }  // namespace
+
+void launch_hist_scan(const u32 *hist, u32 *base, int rows, cudaStream_t s)
+{
+    hist_scan_kernel<<<rows, RADIX, 0, s>>>(hist, base);
+}
 
 void launch_hist_weights(const float *w, i64 n, u32 *hist, int *status, cudaStream_t s)
 {
