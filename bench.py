@@ -608,6 +608,7 @@ def main():
     sampler.stop()
     prof = pd.profile_read()
     timing_note = "CUDA events inside the timed region"
+    graph_ms = None
     if args.async_api:
         # the asynchronous path only counts launches; time the kernels on
         # blocking calls of the same tree right after the timed region
@@ -621,6 +622,29 @@ def main():
             e["launches_async"] = None
         timing_note = ("kernel split from blocking calls after the timed region; "
                        f"{launches_async} kernel launches in the timed region")
+        # the same call captured once in a CUDA graph and replayed
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            pd.dendrogram_async(u, v, w, ws, (ep, vp))
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            pd.dendrogram_async(u, v, w, ws, (ep, vp))
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        ga = torch.cuda.Event(enable_timing=True)
+        gb = torch.cuda.Event(enable_timing=True)
+        ga.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        gb.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = ga.elapsed_time(gb) / args.steps
+        pd.workspace_status(ws)
+        del g
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = sum(step_ms) / len(step_ms)
     if dist:
@@ -677,6 +701,7 @@ def main():
         "kernels": kernels,
         "kernel_timing": timing_note,
         "api": "pandora_dendrogram_async" if args.async_api else "pandora_dendrogram",
+        "graph_ms_per_step": graph_ms if args.async_api else None,
         "levels": stats["level_edges"],
         "clocks": sampler.summary(),
     }

@@ -293,7 +293,6 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         return PANDORA_ERR_WORKSPACE_TOO_SMALL;
     char *base = (char *)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
     Ctrl *ctrl = (Ctrl *)(base + L.ctrl);
-    static_assert(sizeof(Ctrl) > 0, "");
     u32 *keysA = (u32 *)(base + L.keysA), *keysB = (u32 *)(base + L.keysB);
     u32 *valsA = (u32 *)(base + L.valsA), *valsB = (u32 *)(base + L.valsB);
     u32 *perm = (u32 *)(base + L.perm);
