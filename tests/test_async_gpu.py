@@ -119,3 +119,15 @@ def test_graph_capture_and_replay(pd):
         oep, ovp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)
         np.testing.assert_array_equal(ep.cpu().numpy(), oep)
         np.testing.assert_array_equal(vp.cpu().numpy(), ovp)
+
+
+def test_async_above_bucketed_marking_threshold(pd):
+    """An asynchronous call on 4*10^7 vertices: levels are enqueued for their
+    worst-case sizes, so levels 0 and 1 both mark by buckets (more than 2^25
+    vertices each), the second with its records in the sort buffers; every
+    element against the oracle."""
+    t = inputs.rrt(40_000_000, 21)
+    ep, vp = _async_single(pd, t)
+    oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
+    np.testing.assert_array_equal(ep, oep)
+    np.testing.assert_array_equal(vp, ovp)
