@@ -122,11 +122,11 @@ def test_graph_capture_and_replay(pd):
 
 
 def test_async_above_bucketed_marking_threshold(pd):
-    """An asynchronous call on 4*10^7 vertices: levels are enqueued for their
-    worst-case sizes, so levels 0 and 1 both mark by buckets (more than 2^25
-    vertices each), the second with its records in the sort buffers; every
-    element against the oracle."""
-    t = inputs.rrt(40_000_000, 21)
+    """An asynchronous call on 7*10^7 vertices: levels are enqueued for their
+    worst-case sizes (level 1: m/2 + 1 vertices), so levels 0 and 1 both mark
+    by buckets (more than 2^25 vertices each), the second with its records in
+    the sort buffers; every element against the oracle."""
+    t = inputs.rrt(70_000_000, 21)
     ep, vp = _async_single(pd, t)
     oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
     np.testing.assert_array_equal(ep, oep)
