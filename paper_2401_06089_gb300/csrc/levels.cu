@@ -126,9 +126,10 @@ __global__ void __launch_bounds__(256) mark_kernel(const LevelParams p)
         // A plain read first keeps hub vertices (stars) from serialising on one
         // address: the word only decreases, so a stale read may cost an unneeded
         // atomic but never a wrong skip.
-        if (p.min_word[e.x] > wa)
+        const u64 oa = p.min_word[e.x], ob = p.min_word[e.y];   // both reads before the atomics
+        if (oa > wa)
             atomicMin((unsigned long long *)(p.min_word + e.x), (unsigned long long)wa);
-        if (p.min_word[e.y] > wb)
+        if (ob > wb)
             atomicMin((unsigned long long *)(p.min_word + e.y), (unsigned long long)wb);
     }
 }
@@ -307,16 +308,26 @@ __global__ void __launch_bounds__(256) mark_apply_kernel(const LevelParams p)
         const i64 c = s_tile;
         if (c >= chunks)
             break;
+        // all loads of the chunk first, then the atomics: an atomic between
+        // two loads of the word array would order them (they may alias)
+        u32 x[MB_TILE_ITEMS];
+        u64 w[MB_TILE_ITEMS], old[MB_TILE_ITEMS];
 #pragma unroll
         for (int it = 0; it < MB_TILE_ITEMS; ++it) {
             const i64 j = c * MB_TILE + it * 256 + threadIdx.x;
+            x[it] = 0xFFFFFFFFu;
             if (j < total) {
-                const u32 x = p.rec_x[j];
-                const u64 w = p.rec_w[j];
-                if ((i64)x < n && p.min_word[x] > w)
-                    atomicMin((unsigned long long *)(p.min_word + x), (unsigned long long)w);
+                x[it] = p.rec_x[j];
+                w[it] = p.rec_w[j];
             }
         }
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it)
+            old[it] = (i64)x[it] < n ? p.min_word[x[it]] : 0ull;
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it)
+            if ((i64)x[it] < n && old[it] > w[it])
+                atomicMin((unsigned long long *)(p.min_word + x[it]), (unsigned long long)w[it]);
     }
 }
 
