@@ -335,16 +335,18 @@ def run_batched(args):
         torch.cuda.synchronize()
         pd.workspace_status(ws)
         graph = torch.cuda.CUDAGraph()
+        pd.profile_start(timing=False)   # counts the kernels the graph holds
         with torch.cuda.graph(graph):
             call(kind)
+        kernels = sum(e["kernels"] for e in pd.profile_read().values())
         for _ in range(2):
             graph.replay()
         torch.cuda.synchronize()
         pd.workspace_status(ws)
-        return graph
+        return graph, kernels
 
     # the forest-only graph, for comparison (not the headline)
-    g_forest = capture("async")
+    g_forest, _ = capture("async")
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -354,7 +356,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     forest_graph_ms = ev0.elapsed_time(ev1) / args.steps
     del g_forest
-    g = capture("planned")
+    g, graph_kernels = capture("planned")
     gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
     sampler = ClockSampler(gpu_id)
     time.sleep(0.6)
@@ -444,7 +446,8 @@ def run_batched(args):
         "per_tree_async_ms": per_tree_async_ms,
         "speedup_vs_per_tree_blocking": per_tree_blocking_ms / ms,
         "speedup_vs_per_tree_async": per_tree_async_ms / ms,
-        "gpu_launches_per_step": sum(e["kernels"] for e in prof.values()) / args.steps,
+        "gpu_launches": graph_kernels * args.steps,
+        "gpu_launches_per_step": graph_kernels,
         "blocking_kernel_ms": blocking_ms,
         "blocking_dispatch_ms": dispatch_ms,
         "forest_async_graph_ms": forest_graph_ms,
@@ -521,8 +524,10 @@ def run_serving(args):
     sampler = ClockSampler(gpu_id)
     time.sleep(0.6)
     sampler.start()
+    pd.profile_start(timing=False)
     res, wall, server = serve(reqs, arr)
     sampler.stop()
+    serve_kernels = sum(e["kernels"] for e in pd.profile_read().values())
     res = [r for r in res if r.rid >= 200]
     lat = np.array([r.latency for r in res]) * 1e3
     served_edges = sum(r.edge_parent.numel() for r in res)
@@ -542,6 +547,7 @@ def run_serving(args):
         "per_request_blocking_edges_per_s": per_req_rate,
         "speedup_saturated_vs_per_request": sat / per_req_rate,
         "max_batches_in_flight": server.max_inflight,
+        "gpu_launches": serve_kernels,
         "clocks": sampler.summary(),
     }
     if rank == 0:
