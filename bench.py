@@ -162,7 +162,8 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
-# ---- algorithmic bytes per kernel (the model stated in the design doc) ---------
+# ---- algorithmic bytes per kernel: each element touch counted once, a random
+# 4-byte access as 4 bytes (the roofline numerator) ---------------------------
 def sort_weight_bytes(m, launches):
     """Bytes of the (weight, index) sort passes, which carry the endpoints:
     first pass 28 B/edge (read w, u, v; write key, index, u, v), middle 32
@@ -429,6 +430,27 @@ def run_batched(args):
     z.record(stream)
     torch.cuda.synchronize()
     per_tree_async_ms = a.elapsed_time(z)
+    parity = None
+    if args.check:
+        # sampled parity at full size: 16 trees (the largest included) against
+        # the oracle one by one, from the planned graph's outputs
+        import oracle
+        oracle.build()
+        g.replay()
+        torch.cuda.synchronize()
+        pd.workspace_status(ws)
+        ep_h, vp_h = ep.cpu().numpy(), vp.cpu().numpy()
+        rng = np.random.default_rng(spec["seed"] + 99)
+        sizes = np.diff(b.edge_offsets)
+        pick = sorted(set(rng.choice(b.n_trees, size=min(15, b.n_trees), replace=False).tolist()
+                          + [int(np.argmax(sizes))]))
+        ok = True
+        for t in pick:
+            e0, e1 = int(b.edge_offsets[t]), int(b.edge_offsets[t + 1])
+            oep, ovp = oracle.dendrogram(b.u[e0:e1], b.v[e0:e1], b.w[e0:e1])
+            ok = ok and np.array_equal(ep_h[e0:e1], oep) and \
+                np.array_equal(vp_h[e0 + t:e1 + t + 1], ovp)
+        parity = {"oracle": "kruskal", "trees_checked": len(pick), "equal": bool(ok)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -452,6 +474,7 @@ def run_batched(args):
         "blocking_dispatch_ms": dispatch_ms,
         "forest_async_graph_ms": forest_graph_ms,
         "tuning": tuning,
+        "parity": parity,
         "blocking_kernels": kern,
         "levels": bstats["level_edges"],
         "clocks": sampler.summary(),
