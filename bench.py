@@ -178,6 +178,7 @@ def sort_weight_bytes(m, launches):
 
 # per element of the kernel's launch size (edges or vertices of the level)
 MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark": 24,
+               "tail_levels": 25,
                "ptr_init": 28, "compress": 16, "compact": 35, "expand": 25, "link": 16,
                "check_offsets": 16, "fill": 4}
 

@@ -202,6 +202,32 @@ int small_layout_capacity(i64 max_edges);
 // One block per tree; every tree the launch covers has at most max_edges edges.
 void launch_small(const SmallParams &p, int threads, i64 max_edges, unsigned blocks,
                   cudaStream_t s);
+// The last levels of a single tree in one block: once a level has at most
+// TAIL_CAP edges, one block runs that level and every later one in shared
+// memory (Eq. 1, Eq. 2, Section 3.2) and writes what the expansion reads:
+// the contraction level and supervertex of every edge it contracts, the
+// {chain key, supervertex} record of every vertex of each level, and the
+// level sizes and level count in the control block.
+constexpr int TAIL_CAP = 4096;
+constexpr int TAIL_MAX_LEVELS = 16;
+struct TailParams {
+    int level;              // first level the block runs
+    const u64 *d_m;         // Ctrl::lvl_m (indexed by level)
+    u64 *lvl_m;
+    u64 *lvl_n;
+    int *d_n_levels;        // Ctrl::n_levels; nonzero: an earlier level ended the loop
+    const int2 *ab;         // the level's edges (level vertex ids), ascending rank
+    const u32 *er;          // their global ranks
+    i64 ab_cap;             // capacity of ab / er
+    unsigned char *lev;     // [M] contraction level of every edge
+    i32 *start;             // [M] supervertex on the next level
+    int2 *rec[TAIL_MAX_LEVELS];   // records of levels level .. level + TAIL_MAX_LEVELS - 1
+    i64 rec_cap[TAIL_MAX_LEVELS];
+    int max_levels;         // bound on the levels of the whole loop
+    int *status;
+};
+void launch_tail(const TailParams &p, cudaStream_t s);
+
 // Size classes of a batched call: 0..12 = single-block buckets (2^k <= m <
 // 2^(k+1); bucket 0 also takes m = 0), 13 = trees for the forest pipeline.
 constexpr int N_CLASSES = 14;

@@ -23,13 +23,14 @@ namespace {
 // ---- optional instrumentation (pandora_profile_*) -------------------------
 enum Slot : int {
     K_HIST_WEIGHTS, K_SORT_WEIGHTS, K_MARK, K_PTR_INIT, K_COMPRESS, K_COMPACT, K_EXPAND,
-    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_INIT_LEVEL, K_SMALL, K_GATHER, K_SLOTS
+    K_SORT_CHAINS, K_LINK, K_CHECK_OFFSETS, K_FILL, K_INIT_LEVEL, K_SMALL, K_GATHER, K_TAIL,
+    K_SLOTS
 };
 static_assert(K_SLOTS <= PANDORA_PROFILE_SLOTS, "profile slots");
 const char *const kSlotNames[K_SLOTS] = {
     "hist_weights", "onesweep_weights", "mark", "ptr_init", "compress", "compact", "expand",
     "onesweep_chains", "link", "check_offsets", "fill", "init_level", "small_tree",
-    "gather_scatter"};
+    "gather_scatter", "tail_levels"};
 
 struct Profiler {
     std::mutex mu;
@@ -256,6 +257,8 @@ int level_bound(i64 M)
 //             so the call can be captured in a CUDA graph; kernels of levels
 //             past the last one exit at once.  The device status stays in the
 //             workspace (pandora_workspace_status).
+pandora_tuning tuning_snapshot();
+
 // Hooks of the host-buffer entry point: the stream waits for uv_ready (the
 // endpoints' host-to-device copy) only before the first sort pass, which is
 // the first step that reads them; vp_done is recorded once level 0 has
@@ -416,7 +419,48 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     LevelTable table{};
     int n_levels = 0;
     bool useX = true;
+    // the last levels of a single tree run in one block once a level has at
+    // most TAIL_CAP edges (exactly known when blocking, a bound otherwise)
+    const bool tail_ok = T == 1 && !stats && tuning_snapshot().small_max_edges > 0;
+    bool tail_done = false;
     for (int l = 0; l < L_bound; ++l) {
+        if (tail_ok && l >= 1 && m_cap <= TAIL_CAP) {
+            TailParams Q{};
+            Q.level = l;
+            Q.d_m = ctrl->lvl_m;
+            Q.lvl_m = ctrl->lvl_m;
+            Q.lvl_n = ctrl->lvl_n;
+            Q.d_n_levels = &ctrl->n_levels;
+            Q.ab = ab;
+            Q.er = er;
+            Q.ab_cap = L.half_cap;
+            Q.lev = lev;
+            Q.start = start;
+            Q.max_levels = L_bound;
+            Q.status = status;
+            int k = 0;
+            for (; k < TAIL_MAX_LEVELS && l + k < L_bound; ++k) {
+                const i64 cap = (m_cap >> k) + T;
+                if (kept_used + cap > L.kept_cap)
+                    break;
+                Q.rec[k] = kept_rec + kept_used;
+                Q.rec_cap[k] = cap;
+                table.rec[l + k] = Q.rec[k];
+                table.n_cap[l + k] = cap;
+                kept_used += cap;
+            }
+            timer.launch(K_TAIL, m_cap, [&] { launch_tail(Q, s); });
+            PANDORA_CUDA(cudaGetLastError());
+            n_levels = l + k;
+            tail_done = true;
+            if (blocking) {
+                if (int e = read_counters(ctrl, &h, s))
+                    return e;
+                if (h.status)
+                    return h.status;
+            }
+            break;
+        }
         LevelParams P{};
         P.level = l;
         P.d_m = &ctrl->lvl_m[l];
@@ -527,6 +571,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     }
     if (blocking && h.n_levels == 0)
         return PANDORA_ERR_NOT_A_TREE;   // the level bound of Section 4.2 was exceeded
+    (void)tail_done;
 
     // ---- 3. expansion: chain key of every edge -----------------------------
     const u32 root_base = (u32)(2 * M);

@@ -411,6 +411,166 @@ void launch_small_cap(const SmallParams &p, int threads, unsigned blocks, cudaSt
     }
 }
 
+// ---- the last levels of a single tree in one block ---------------------------
+struct TailSmem {
+    unsigned short ea[TAIL_CAP], eb[TAIL_CAP];   // endpoints (level ids < n <= TAIL_CAP + 1)
+    u32 er[TAIL_CAP];                            // global ranks
+    unsigned short na[TAIL_CAP / 2], nb[TAIL_CAP / 2];
+    u32 nr[TAIL_CAP / 2];
+    u32 word[TAIL_CAP + 1];                      // (local index << 14 | other << 1 | side)
+    short ptr[TAIL_CAP + 1];
+    unsigned short vmap[TAIL_CAP + 1];
+    u32 warp_tot[32];
+    u32 counts[4];
+};
+
+// Edges of a level are listed in ascending global rank, so a local index
+// orders them as the rank does and the lightest-edge word fits 32 bits.
+__global__ void __launch_bounds__(1024) tail_levels_kernel(const TailParams p)
+{
+    constexpr int T = 1024;
+    if (*(const volatile int *)p.d_n_levels != 0)
+        return;   // the loop ended on an earlier level
+    extern __shared__ __align__(16) unsigned char tail_raw[];
+    TailSmem *s = (TailSmem *)tail_raw;
+    const int tid = threadIdx.x;
+    const i64 m64 = (i64)p.d_m[p.level];
+    if (m64 > TAIL_CAP || m64 < 0 || m64 > p.ab_cap) {
+        if (tid == 0)
+            set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // more than the bound allows
+        return;
+    }
+    int ml = (int)m64, nl = ml + 1;
+    for (int i = tid; i < ml; i += T) {
+        const int2 e = p.ab[i];
+        const bool ok = e.x >= 0 && e.x < nl && e.y >= 0 && e.y < nl;
+        s->ea[i] = (unsigned short)(ok ? e.x : 0);
+        s->eb[i] = (unsigned short)(ok ? e.y : 0);
+        s->er[i] = p.er[i];
+        if (!ok)
+            set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+    }
+    __syncthreads();
+    for (int k = 0;; ++k) {
+        const int level = p.level + k;
+        if (k >= TAIL_MAX_LEVELS || level >= p.max_levels || (i64)nl > p.rec_cap[k]) {
+            if (tid == 0)
+                set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // beyond Section 4.2's bound
+            return;
+        }
+        if (tid == 0) {
+            p.lvl_m[level] = (u64)ml;
+            p.lvl_n[level] = (u64)nl;
+        }
+        // Eq. 1
+        for (int x = tid; x < nl; x += T)
+            s->word[x] = W_NONE;
+        __syncthreads();
+        for (int i = tid; i < ml; i += T) {
+            const u32 a = s->ea[i], b = s->eb[i];
+            atomicMin(&s->word[a], ((u32)i << 14) | (b << 1));
+            atomicMin(&s->word[b], ((u32)i << 14) | (a << 1) | 1u);
+        }
+        __syncthreads();
+        // pointer forest, roots with dense ids in vertex order
+        const int vper = (nl + T - 1) / T;
+        const int v0 = tid * vper;
+        u32 local = 0;
+        for (int x = v0; x < v0 + vper && x < nl; ++x) {
+            const u32 wx = s->word[x];
+            const u32 y = (wx >> 1) & 0x1FFFu;
+            const bool root = wx == W_NONE || (((s->word[y] >> 14) == (wx >> 14)) && ((u32)x < y));
+            local += root ? 1u : 0u;
+        }
+        u32 rank = block_rank_start<T>(s, local, 0);
+        const int n_next = (int)s->counts[0];
+        for (int x = v0; x < v0 + vper && x < nl; ++x) {
+            const u32 wx = s->word[x];
+            const u32 y = (wx >> 1) & 0x1FFFu;
+            const bool root = wx == W_NONE || (((s->word[y] >> 14) == (wx >> 14)) && ((u32)x < y));
+            s->ptr[x] = root ? (short)~(int)rank++ : (short)y;
+        }
+        __syncthreads();
+        for (int x = tid; x < nl; x += T) {
+            int cur = x, res = ~0;
+            volatile short *vptr = s->ptr;
+            for (int it = 0; it <= nl; ++it) {
+                const int pc = vptr[cur];
+                if (pc < 0) {
+                    res = pc;
+                    break;
+                }
+                const int g = vptr[pc];
+                if (g < 0) {
+                    res = g;
+                    break;
+                }
+                vptr[cur] = (short)g;
+                cur = g;
+            }
+            s->vmap[x] = (unsigned short)~res;
+        }
+        __syncthreads();
+        // the records the expansion walks: {2 * rank + side of x's lightest
+        // edge, x's supervertex on the next level}
+        for (int x = tid; x < nl; x += T) {
+            const u32 wx = s->word[x];
+            const u32 ck = wx == W_NONE ? NONE : 2u * s->er[wx >> 14] + (wx & 1u);
+            p.rec[k][x] = make_int2((i32)ck, (i32)s->vmap[x]);
+        }
+        // Eq. 2: alpha-edges go on, the others are contracted on this level
+        const int eper = (ml + T - 1) / T;
+        const int i0 = tid * eper;
+        local = 0;
+        for (int i = i0; i < i0 + eper && i < ml; ++i) {
+            const bool alpha = (s->word[s->ea[i]] >> 14) != (u32)i &&
+                               (s->word[s->eb[i]] >> 14) != (u32)i;
+            local += alpha ? 1u : 0u;
+        }
+        rank = block_rank_start<T>(s, local, 1);
+        const int m_next = (int)s->counts[1];
+        for (int i = i0; i < i0 + eper && i < ml; ++i) {
+            const int a = s->ea[i], b = s->eb[i];
+            const bool alpha = (s->word[a] >> 14) != (u32)i && (s->word[b] >> 14) != (u32)i;
+            if (alpha) {
+                if (s->vmap[a] == s->vmap[b])
+                    set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+                if (rank < TAIL_CAP / 2) {
+                    s->na[rank] = s->vmap[a];
+                    s->nb[rank] = s->vmap[b];
+                    s->nr[rank] = s->er[i];
+                }
+                ++rank;
+            } else {
+                p.lev[s->er[i]] = (unsigned char)level;
+                p.start[s->er[i]] = (i32)s->vmap[a];
+            }
+        }
+        __syncthreads();
+        if (n_next != m_next + 1 || m_next > TAIL_CAP / 2) {
+            if (tid == 0)
+                set_status(p.status, PANDORA_ERR_NOT_A_TREE);
+            return;
+        }
+        if (m_next == 0) {
+            if (tid == 0) {
+                p.lvl_m[level + 1] = 0;
+                p.lvl_n[level + 1] = 1;
+                *p.d_n_levels = level + 1;
+            }
+            return;
+        }
+        for (int i = tid; i < m_next; i += T) {
+            s->ea[i] = s->na[i];
+            s->eb[i] = s->nb[i];
+            s->er[i] = s->nr[i];
+        }
+        __syncthreads();
+        ml = m_next;
+        nl = n_next;
+    }
+}
+
 // Copies the edges of the trees in `list` into a packed forest (offsets
 // `coff`): one thread per packed edge (a binary search over coff finds its
 // tree), so a few large trees still spread over the whole GPU.
@@ -587,6 +747,21 @@ int small_tree_capacity() { return SMALL_CAP; }
 int small_layout_capacity(i64 max_edges)
 {
     return max_edges < 256 ? 256 : max_edges < 1024 ? 1024 : SMALL_CAP;
+}
+
+void launch_tail(const TailParams &p, cudaStream_t s)
+{
+    const int bytes = (int)sizeof(TailSmem);
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load() & bit)) {
+        cudaFuncSetAttribute(tail_levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+        done.fetch_or(bit);
+    }
+    tail_levels_kernel<<<1, 1024, bytes, s>>>(p);
 }
 
 void launch_plan(const PlanParams &p, cudaStream_t s)
