@@ -89,6 +89,38 @@ class _Runner:
         return self.ep.cpu().numpy(), self.vp.cpu().numpy()
 
 
+def choose_threads_and_cutoff(buckets):
+    """Fastest block size per bucket; the cutoff is the top of the last bucket,
+    counting up from bucket 0, in which the solver beats the pipeline."""
+    threads = [row["best_threads"] for row in buckets]
+    cutoff = 0
+    for row in buckets:
+        if row["solver_ms"][str(row["best_threads"])] < row["pipeline_ms"]:
+            cutoff = min(CAP, (1 << (row["bucket"] + 1)) - 1)
+        else:
+            break
+    return threads, cutoff
+
+
+def choose_split_permille(buckets, cutoff, pack_ns_per_large_edge):
+    """Split a mixed batch when its small trees hold at least the share s of
+    its edges at which the saving equals the packing cost:
+    s * saving = (1 - s) * pack, with saving the median (pipeline - solver)
+    time per edge over the buckets under the cutoff.  Returns (saving, per
+    mille); no saving means never split a mixed batch (1000)."""
+    small_rows = [row for row in buckets if row["bucket"] >= 1 and
+                  (1 << row["bucket"]) <= max(cutoff, 1)]
+    if small_rows:
+        saving = float(np.median([row["pipeline_ns_per_edge"] - row["solver_ns_per_edge"]
+                                  for row in small_rows]))
+    else:
+        saving = 0.0
+    if saving <= 0:
+        return saving, 1000
+    g = pack_ns_per_large_edge
+    return saving, int(min(max(math.ceil(1000 * g / (g + saving) - 1e-9), 0), 1000))
+
+
 def tune(target_edges: int = 2_000_000, seed: int = 7, verbose: bool = True) -> dict:
     import torch
     B.load_library()
@@ -127,13 +159,7 @@ def tune(target_edges: int = 2_000_000, seed: int = 7, verbose: bool = True) -> 
             del r
             torch.cuda.empty_cache()
 
-        threads = [row["best_threads"] for row in buckets]
-        cutoff = 0
-        for row in buckets:
-            if row["solver_ms"][str(row["best_threads"])] < row["pipeline_ms"]:
-                cutoff = min(CAP, (1 << (row["bucket"] + 1)) - 1)
-            else:
-                break
+        threads, cutoff = choose_threads_and_cutoff(buckets)
 
         # split threshold: packing cost per large-tree edge against the saving
         # per small-tree edge, on a batch of a few large trees and many small ones
@@ -153,17 +179,7 @@ def tune(target_edges: int = 2_000_000, seed: int = 7, verbose: bool = True) -> 
         large_edges = int(8 * 500_000)
         pack_ms = (prof.get("gather_scatter", {}).get("ms") or 0.0) / 3
         g = 1e6 * pack_ms / large_edges                   # ns per large-tree edge
-        small_rows = [row for row in buckets if row["bucket"] >= 1 and
-                      (1 << row["bucket"]) <= max(cutoff, 1)]
-        if small_rows:
-            saving = float(np.median([row["pipeline_ns_per_edge"] - row["solver_ns_per_edge"]
-                                      for row in small_rows]))
-        else:
-            saving = 0.0
-        if saving <= 0:
-            permille = 1000
-        else:
-            permille = int(math.ceil(1000 * g / (g + saving)))
+        saving, permille = choose_split_permille(buckets, cutoff, g)
         result = {
             "small_max_edges": int(cutoff),
             "small_threads": [int(t) for t in threads],
