@@ -120,12 +120,8 @@ class DendrogramServer:
         self.poll()
         admitted = 0
         while self.free_streams:
-            if self.pending_small:
-                lane = self.pending_small
-            elif self.pending and (len(self.free_streams) > 1 or not self.inflight
-                                   or self.small_cutoff < 0):
-                lane = self.pending   # large batches leave one stream for small requests
-            else:
+            lane = self._pick_lane()
+            if lane is None:
                 break
             reqs = self._take(lane)
             if not reqs:
@@ -133,6 +129,17 @@ class DendrogramServer:
             self._launch(reqs)
             admitted += 1
         return admitted
+
+    def _pick_lane(self):
+        """The lane to admit from next: small requests first; a large batch
+        never takes the last free stream while other batches run (a small
+        request arriving meanwhile would wait behind it)."""
+        if self.pending_small:
+            return self.pending_small
+        if self.pending and (len(self.free_streams) > 1 or not self.inflight
+                             or self.small_cutoff < 0):
+            return self.pending
+        return None
 
     def _take(self, lane: deque) -> List[Request]:
         free = self.budget - self.bytes_in_use
