@@ -64,7 +64,14 @@ typedef enum pandora_status {
     PANDORA_ERR_OUT_OF_MEMORY = 7,      /* scratch allocation failed */
     PANDORA_ERR_CUDA = 8,               /* a CUDA runtime call failed */
     PANDORA_ERR_WORKSPACE_TOO_SMALL = 9,/* caller workspace below pandora_workspace_size() */
-    PANDORA_ERR_SIZE_LIMIT = 10         /* n_edges above PANDORA_NOALLOC_MAX_EDGES */
+    PANDORA_ERR_SIZE_LIMIT = 10,        /* n_edges above PANDORA_NOALLOC_MAX_EDGES, or
+                                           n_vertices above PANDORA_FLAT_MAX_VERTICES */
+    PANDORA_ERR_BAD_WEIGHT = 11,        /* flat clusters: a weight is not positive and
+                                           finite (lambda = 1 / w is needed) */
+    PANDORA_ERR_NOT_A_DENDROGRAM = 12   /* flat clusters: the parent arrays are not a
+                                           binary tree with one root in which every
+                                           edge comes after its children in the
+                                           (weight, index) order */
 } pandora_status;
 
 /* Per-call statistics (optional output of the *_ws entry points). */
@@ -293,6 +300,45 @@ typedef struct pandora_profile {
 
 int pandora_profile_start(int with_timing);
 int pandora_profile_read(pandora_profile *out);
+
+/*
+ * HDBSCAN* flat clusters of a dendrogram (the optional last step of the
+ * HDBSCAN* pipeline, Section 6.5, as defined by Campello et al.).
+ *
+ * Input: a dendrogram of n_vertices = m + 1 points as produced by
+ * pandora_dendrogram (device arrays): edge_parent[m] (-1 at the root edge),
+ * vertex_parent[n_vertices] and the weights w[m] (positive and finite;
+ * lambda(e) = 1 / w(e) in float64).  As edges are removed from the heaviest
+ * down, a cluster is a part of the tree that stays at least min_cluster_size
+ * points large: it is born where its part splits off (the whole tree at
+ * lambda 0), ends where it splits into two such parts, and loses the points
+ * that fall off in smaller parts.  Its stability is the sum over its points
+ * of (lambda at which the point leaves it - lambda at its birth), each term
+ * in float64, summed exactly and rounded once (so the value does not depend
+ * on any order).  Excess of mass: over all clusters but the whole tree, from
+ * the leaves of the cluster tree up, a cluster is kept instead of the best
+ * set found under it when its stability is at least that set's total (the
+ * total of two float64 values, rounded once).
+ *
+ * Output: labels[n_vertices] (device): the kept cluster that contains the
+ * point, numbered 0, 1, ... in increasing order of each cluster's smallest
+ * point id, or -1 for noise.  cluster_stability (device, optional, NULL to
+ * skip): room for n_vertices / min_cluster_size doubles; entry k receives
+ * the stability of cluster k.  n_clusters (host, optional): the number of
+ * kept clusters.
+ *
+ * min_cluster_size >= 2 (else PANDORA_ERR_INVALID_ARGUMENT); at most
+ * PANDORA_FLAT_MAX_VERTICES points (else PANDORA_ERR_SIZE_LIMIT).  The input
+ * is validated on the device: PANDORA_ERR_BAD_WEIGHT,
+ * PANDORA_ERR_NOT_A_DENDROGRAM.  Scratch (about 105 bytes per point plus
+ * 180 bytes per possible cluster, 2 n_vertices / min_cluster_size + 1)
+ * comes from the library's stream-ordered pool.  Blocking: returns after the work on `stream` has finished.
+ */
+#define PANDORA_FLAT_MAX_VERTICES 536870912
+int pandora_hdbscan_labels(const int32_t *edge_parent, const int32_t *vertex_parent,
+                           const float *w, int64_t n_vertices, int32_t min_cluster_size,
+                           int32_t *labels, double *cluster_stability, int64_t *n_clusters,
+                           void *stream);
 
 /* Static description of a status code (never NULL). */
 const char *pandora_status_string(int status);

@@ -52,7 +52,8 @@ def hdbscan_labels(edge_parent, vertex_parent, w, min_cluster_size, members: boo
     """Returns (labels int32[n], info) for a dendrogram of m edges and
     n = m + 1 vertices.  info["clusters"]: per cluster (in creation order,
     cluster 0 the root) its starting node ("e", edge) or the root edge, parent
-    cluster, birth lambda, size, stability, score and selection; with
+    cluster, birth lambda, size, stability, score, selection and label (-1
+    unless selected); with
     ``members`` also its sorted vertex ids."""
     ep = np.asarray(edge_parent, dtype=np.int64)
     vp = np.asarray(vertex_parent, dtype=np.int64)
@@ -181,6 +182,7 @@ def hdbscan_labels(edge_parent, vertex_parent, w, min_cluster_size, members: boo
     for ci, C in enumerate(clusters):
         C["selected"] = selected[ci]
         C["score"] = score[ci]
+        C["label"] = rank.get(ci, -1)
         if members:
             C["members"] = sorted(leaves("e", C["edge"]))   # sizes >= mcs >= 2: edges
     return labels, {"clusters": clusters}

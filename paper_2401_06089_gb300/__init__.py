@@ -15,6 +15,7 @@ from ._binding import (  # noqa: F401
     dendrogram_batched_planned,
     dendrogram_host,
     get_tuning,
+    hdbscan_labels,
     library_path,
     load_tuning,
     profile_read,

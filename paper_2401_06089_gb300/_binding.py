@@ -31,7 +31,11 @@ STATUS_NAMES = {
     8: "PANDORA_ERR_CUDA",
     9: "PANDORA_ERR_WORKSPACE_TOO_SMALL",
     10: "PANDORA_ERR_SIZE_LIMIT",
+    11: "PANDORA_ERR_BAD_WEIGHT",
+    12: "PANDORA_ERR_NOT_A_DENDROGRAM",
 }
+
+FLAT_MAX_VERTICES = 536870912   # PANDORA_FLAT_MAX_VERTICES
 
 SMALL_CAP = 4096          # largest tree the single-block solver takes
 SMALL_BUCKETS = 13        # bucket k: trees with 2^k <= m < 2^(k+1) edges (k = 0 also m = 0)
@@ -99,12 +103,15 @@ def load_library():
         lib.pandora_profile_read.argtypes = [P]
         lib.pandora_set_tuning.argtypes = [P]
         lib.pandora_get_tuning.argtypes = [P]
+        lib.pandora_hdbscan_labels.argtypes = [P, P, P, I64, ctypes.c_int32, P, P,
+                                               ctypes.POINTER(I64), P]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
                      "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
-                     "pandora_dendrogram_batched_planned", "pandora_dendrogram_host"):
+                     "pandora_dendrogram_batched_planned", "pandora_dendrogram_host",
+                     "pandora_hdbscan_labels"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     _apply_default_tuning()
@@ -272,6 +279,42 @@ def dendrogram(u, v, w, *, workspace=None, stats: bool = False, out=None):
     if stats:
         return ep, vp, _stats_dict(st_out)
     return ep, vp
+
+
+def hdbscan_labels(edge_parent, vertex_parent, w, min_cluster_size: int, *,
+                   stability: bool = False):
+    """HDBSCAN* flat clusters of a dendrogram (``pandora_hdbscan_labels``).
+
+    ``edge_parent`` (int32[m]), ``vertex_parent`` (int32[m + 1]) and ``w``
+    (float32[m], positive) are CUDA tensors, e.g. the outputs of
+    ``dendrogram`` and its weights.  Returns int32 labels (-1 = noise,
+    clusters numbered by their smallest point id); with ``stability`` also
+    the float64 stability of every cluster, indexed by label.
+    """
+    torch = _torch()
+    lib = load_library()
+    _check(vertex_parent, torch.int32, "vertex_parent")
+    dev = vertex_parent.device
+    n = vertex_parent.numel()
+    m = max(n - 1, 0)
+    _check(edge_parent, torch.int32, "edge_parent", dev, m)
+    _check(w, torch.float32, "w", dev, m)
+    mcs = int(min_cluster_size)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    stab = None
+    if stability:
+        stab = torch.empty(max(n // max(mcs, 1), 1), dtype=torch.float64, device=dev)
+    nc = ctypes.c_int64(0)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_hdbscan_labels(_ptr(edge_parent), _ptr(vertex_parent), _ptr(w), n, mcs,
+                                        _ptr(labels), _ptr(stab) if stability else None,
+                                        ctypes.byref(nc), stream)
+    if st:
+        raise PandoraError(st, "pandora_hdbscan_labels")
+    if stability:
+        return labels, stab[: nc.value]
+    return labels
 
 
 def dendrogram_host(u, v, w, *, out=None, device=None):

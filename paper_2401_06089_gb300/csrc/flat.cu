@@ -1,0 +1,939 @@
+// HDBSCAN* flat clusters from a single-linkage dendrogram
+// (pandora_hdbscan_labels, include/pandora.h).
+//
+// The optional last step of the HDBSCAN* pipeline (Section 6.5): the flat
+// clustering of Campello et al.  As edges are removed from the heaviest down
+// (lambda = 1/w grows), a cluster is a part of the tree that stays at least
+// min_cluster_size (mcs) points large; it ends where it splits into two such
+// parts, and points leave it where they fall off in smaller parts.  Clusters
+// are scored by their stability and the non-overlapping set of largest total
+// stability is kept (excess of mass, the whole data set excluded).
+//
+// Nodes: edge e is node e, vertex x is node m + x; the parent of a node is
+// edge_parent / vertex_parent.  Every step is a data-parallel kernel:
+//
+//  1. parents, child slots and validation (binary tree, one root, every
+//     parent later than its child in (weight, index) order, weights > 0);
+//  2. leaf counts: Euler tour of the dendrogram (down/up arc per edge, one
+//     arc per leaf), suffix sums by Wyllie pointer jumping;
+//  3. per node: big = leaf count >= mcs; cluster starts (the root, and both
+//     children of an edge whose children are both big); anchors (starts, and
+//     small nodes under a big parent); nearest anchor above every node by
+//     pointer jumping.  A vertex's anchor is the top of the small part it
+//     falls off in; that part's parent edge p gives the leave lambda and the
+//     cluster (p's anchor, a start);
+//  4. stabilities: every term (a leaving point's fl(lambda - birth), and
+//     size(D) copies of a child cluster's fl(birth(D) - birth(C))) is a
+//     multiple of 2^-180 below 2^181 (lambda = 1/w of a float32 w lies in
+//     (2^-128, 2^149]), so it is added exactly into a fixed-point accumulator
+//     of 32-bit digits with integer atomics; the exact sum is rounded once to
+//     float64 (round to nearest, ties to even).  The result does not depend on
+//     the order of the additions;
+//  5. excess of mass bottom-up over the binary cluster tree: the second child
+//     to finish continues with the parent (an atomic arrival count; nothing
+//     waits);
+//  6. labels: the topmost selected cluster above a vertex's cluster (pointer
+//     jumping over the cluster tree), numbered by smallest member (two scans).
+#include <cfloat>
+#include <cstdint>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pandora {
+cudaMemPool_t flat_pool(int dev);
+}
+
+namespace {
+
+using namespace pandora;
+
+constexpr int FT = 256;            // threads per block of the element-wise kernels
+constexpr int NL = 14;             // 32-bit digits of a stability accumulator (448 bits)
+constexpr int FIX_EXP = 180;       // accumulator unit: 2^-180
+constexpr u32 FULL = 0xFFFFFFFFu;
+
+struct FlatCtrl {
+    int status;
+    int n_roots;
+    int root;          // root edge
+    int n_starts;      // clusters (start edges), from the scan
+    int root_cid;      // cluster id of the root
+    int n_selected;    // selected clusters, from the scan
+    int pad[2];
+};
+
+__device__ __forceinline__ bool failed(const FlatCtrl *c)
+{
+    return *(const volatile int *)&c->status != 0;
+}
+
+__device__ __forceinline__ i32 enter_arc(i32 node, i32 m)
+{
+    return node < m ? 2 * node : 2 * m + (node - m);
+}
+
+// Arc after the last arc of node c's subtree walk.
+__device__ __forceinline__ i32 after_arc(i32 c, i32 m, const i32 *par, const i32 *kids)
+{
+    const i32 p = par[c];
+    if (p < 0)
+        return -1;
+    if (kids[2 * (i64)p] == c)
+        return enter_arc(kids[2 * (i64)p + 1], m);
+    return par[p] < 0 ? -1 : 2 * p + 1;
+}
+
+// ---- 1. parents and validation --------------------------------------------
+__global__ void flat_parents_kernel(const i32 *ep, const i32 *vp, const float *w, i32 m, i32 n,
+                                    i32 *par, i32 *cnt, i32 *kids, FlatCtrl *c)
+{
+    const i64 N = (i64)m + n;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
+         i += (i64)gridDim.x * blockDim.x) {
+        i32 p;
+        if (i < m) {
+            const float we = w[i];
+            if (!(we > 0.f && we <= FLT_MAX))
+                set_status(&c->status, PANDORA_ERR_BAD_WEIGHT);
+            p = ep[i];
+            if (p == -1) {
+                atomicAdd(&c->n_roots, 1);
+                c->root = (i32)i;
+                par[i] = -1;
+                continue;
+            }
+        } else {
+            p = vp[i - m];
+        }
+        if (p < 0 || p >= m) {
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+            par[i] = -1;
+            continue;
+        }
+        par[i] = p;
+        const i32 slot = atomicAdd(&cnt[p], 1);
+        if (slot < 2)
+            kids[2 * (i64)p + slot] = (i32)i;
+    }
+}
+
+// Two children per edge, one root, and every parent after its child in the
+// (weight, index) order (which also rules out cycles).
+__global__ void flat_check_kernel(const float *w, i32 m, const i32 *par, const i32 *cnt,
+                                  FlatCtrl *c)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c->n_roots != 1)
+        set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        bool ok = cnt[e] == 2;
+        const i32 p = par[e];
+        if (p >= 0) {
+            const float wp = w[p], we = w[e];
+            ok = ok && (wp > we || (wp == we && p > e));
+        }
+        if (!ok)
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    }
+}
+
+// ---- 2. leaf counts ----------------------------------------------------------
+// Arc word: next arc (high 32 bits, -1 at the end) | leaf count (low 32 bits).
+__global__ void tour_init_kernel(i32 m, i32 n, const i32 *par, const i32 *kids, u64 *arc,
+                                 const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i64 L = 2 * (i64)m + n;
+    for (i64 a = blockIdx.x * (i64)blockDim.x + threadIdx.x; a < L;
+         a += (i64)gridDim.x * blockDim.x) {
+        i32 next;
+        u32 val = 0;
+        if (a < 2 * (i64)m) {
+            const i32 e = (i32)(a >> 1);
+            next = (a & 1) ? after_arc(e, m, par, kids) : enter_arc(kids[2 * (i64)e], m);
+        } else {
+            next = after_arc(m + (i32)(a - 2 * (i64)m), m, par, kids);
+            val = 1;
+        }
+        arc[a] = ((u64)(u32)next << 32) | val;
+    }
+}
+
+__global__ void rank_step_kernel(const u64 *in, u64 *out, i64 L, const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 a = blockIdx.x * (i64)blockDim.x + threadIdx.x; a < L;
+         a += (i64)gridDim.x * blockDim.x) {
+        const u64 r = in[a];
+        const i32 nx = (i32)(r >> 32);
+        if (nx >= 0) {
+            const u64 q = in[nx];
+            out[a] = (q & 0xFFFFFFFF00000000ull) | (u32)((u32)r + (u32)q);
+        } else {
+            out[a] = r;
+        }
+    }
+}
+
+// size(e) = suffix(down(e)) - suffix(up(e)); the root holds all n leaves.
+__global__ void sizes_kernel(const u64 *suf, i32 m, i32 n, i32 *size, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root = c->root;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (u32)suf[2 * (i64)root] != (u32)n)
+        set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x)
+        size[e] = e == root ? n : (i32)((u32)suf[2 * e] - (u32)suf[2 * e + 1]);
+}
+
+// ---- 3. starts and anchors ---------------------------------------------------
+__global__ void anchor_init_kernel(i32 m, i32 n, i32 mcs, const i32 *par, const i32 *kids,
+                                   const i32 *size, i32 *jmp, i32 *start, const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root = c->root;
+    const i64 N = (i64)m + n;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
+         i += (i64)gridDim.x * blockDim.x) {
+        const i32 p = par[i];
+        const bool big = (i < m ? size[i] : 1) >= mcs;
+        bool st = false;
+        if (i == root) {
+            st = true;
+        } else if (big) {
+            const i32 k0 = kids[2 * (i64)p];
+            const i32 sib = k0 == (i32)i ? kids[2 * (i64)p + 1] : k0;
+            st = (sib < m ? size[sib] : 1) >= mcs;
+        }
+        const bool anchor = st || (!big && p >= 0 && size[p] >= mcs);
+        jmp[i] = anchor ? (i32)i : p;
+        if (i < m)
+            start[i] = st;
+    }
+}
+
+// In place: a node only ever moves up its own chain and anchors point to
+// themselves, so any interleaving reaches the synchronous result or further.
+__global__ void jump_kernel(i32 *jmp, i64 N, const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
+         i += (i64)gridDim.x * blockDim.x) {
+        const i32 j = jmp[i];
+        const i32 jj = jmp[j];
+        if (jj != j)
+            jmp[i] = jj;
+    }
+}
+
+// ---- exclusive scan of int32 flags (3 kernels) --------------------------------
+constexpr int SC_ITEMS = 8;
+constexpr int SC_TILE = FT * SC_ITEMS;
+
+__device__ __forceinline__ i32 block_exclusive_scan(i32 v, i32 *sm, i32 *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    i32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const i32 y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        i32 s = lane < nw ? sm[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const i32 y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        sm[lane] = s;
+    }
+    __syncthreads();
+    const i32 before = warp ? sm[warp - 1] : 0;
+    *total = sm[nw - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void scan_reduce_kernel(const i32 *in, i64 len, i32 *bsum)
+{
+    __shared__ i32 sm[32];
+    const i64 base = blockIdx.x * (i64)SC_TILE + threadIdx.x * (i64)SC_ITEMS;
+    i32 s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k)
+        if (base + k < len)
+            s += in[base + k];
+    i32 total;
+    block_exclusive_scan(s, sm, &total);
+    if (threadIdx.x == 0)
+        bsum[blockIdx.x] = total;
+}
+
+// One block: bsum[0..nb) becomes its exclusive scan; *total gets the sum.
+__global__ void scan_top_kernel(i32 *bsum, i64 nb, i32 *total)
+{
+    __shared__ i32 sm[32];
+    const i64 per = (nb + blockDim.x - 1) / blockDim.x;
+    const i64 lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    i32 s = 0;
+    for (i64 i = lo; i < hi; ++i)
+        s += bsum[i];
+    i32 tot;
+    i32 run = block_exclusive_scan(s, sm, &tot);
+    for (i64 i = lo; i < hi; ++i) {
+        const i32 v = bsum[i];
+        bsum[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == 0)
+        *total = tot;
+}
+
+__global__ void scan_down_kernel(const i32 *in, i64 len, const i32 *bsum, i32 *out)
+{
+    __shared__ i32 sm[32];
+    const i64 base = blockIdx.x * (i64)SC_TILE + threadIdx.x * (i64)SC_ITEMS;
+    i32 v[SC_ITEMS];
+    i32 s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        v[k] = base + k < len ? in[base + k] : 0;
+        s += v[k];
+    }
+    i32 total;
+    i32 run = bsum[blockIdx.x] + block_exclusive_scan(s, sm, &total);
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        if (base + k < len)
+            out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// ---- 4. exact stability sums ---------------------------------------------------
+// (host-callable too, so that the arithmetic can be checked without a GPU)
+__host__ __device__ __forceinline__ u64 double_bits(double t)
+{
+#ifdef __CUDA_ARCH__
+    return (u64)__double_as_longlong(t);
+#else
+    u64 b;
+    memcpy(&b, &t, sizeof b);
+    return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double bits_double(u64 b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double t;
+    memcpy(&t, &b, sizeof t);
+    return t;
+#endif
+}
+
+__host__ __device__ __forceinline__ int leading_zeros(u32 x)
+{
+#ifdef __CUDA_ARCH__
+    return __clz(x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// Splits a non-negative double t that is a multiple of 2^-FIX_EXP into digits
+// d[0..2] with t * 2^FIX_EXP = (d0 + d1 * 2^32 + d2 * 2^64) * 2^(32 * j0).
+// Returns false for t == 0; a value outside that form sets *bad.
+__host__ __device__ __forceinline__ bool split_digits(double t, int &j0, u32 &d0, u32 &d1,
+                                                      u32 &d2, bool &bad)
+{
+    const u64 bits = double_bits(t);
+    if ((bits << 1) == 0)
+        return false;
+    const int ex = (int)(bits >> 52);          // sign bit included: negative -> >= 2048
+    if (ex == 0 || ex >= 2047) {
+        bad = true;
+        return false;
+    }
+    u64 M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    int s = ex - 1075 + FIX_EXP;               // t * 2^FIX_EXP = M * 2^s
+    if (s < 0) {
+        const int sh = -s;
+        if (sh >= 53 || (M & ((1ull << sh) - 1))) {
+            bad = true;
+            return false;
+        }
+        M >>= sh;
+        s = 0;
+    }
+    j0 = s >> 5;
+    const int r = s & 31;
+    if (j0 + 2 >= NL) {
+        bad = true;
+        return false;
+    }
+    d0 = (u32)(M << r);
+    const u64 t1 = M >> (32 - r);
+    d1 = (u32)t1;
+    d2 = (u32)(t1 >> 32);
+    return true;
+}
+
+__global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32 *cid,
+                                    const i32 *par, const i32 *jmp, const i32 *size,
+                                    const float *w, i32 *cpar, i32 *ckids, i32 *ccnt, i32 *csize,
+                                    double *birth, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root = c->root;
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        if (!start[e])
+            continue;
+        const i32 k = cid[e];
+        const i32 pk = e == root ? -1 : cid[jmp[par[e]]];
+        if (k >= Kmax || pk >= Kmax) {           // more clusters than n / mcs allows
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+            continue;
+        }
+        csize[k] = size[e];
+        if (e == root) {
+            cpar[k] = -1;
+            birth[k] = 0.0;
+            c->root_cid = k;
+            continue;
+        }
+        birth[k] = 1.0 / (double)w[par[e]];
+        cpar[k] = pk;
+        const i32 slot = atomicAdd(&ccnt[pk], 1);
+        if (slot < 2)
+            ckids[2 * (i64)pk + slot] = k;
+        else
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    }
+}
+
+// size(D) copies of fl(birth(D) - birth(C)), added to C's accumulator.
+__global__ void child_terms_kernel(i32 K, const i32 *cpar, const i32 *csize,
+                                   const double *birth, u64 *acc, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 pk = cpar[k];
+        if (pk < 0)
+            continue;
+        const double d = birth[k] - birth[pk];
+        int j0;
+        u32 dg[3];
+        bool bad = false;
+        if (split_digits(d, j0, dg[0], dg[1], dg[2], bad)) {
+            const u64 mult = (u64)(u32)csize[k];
+            for (int q = 0; q < 3; ++q)
+                if (dg[q])
+                    atomicAdd((unsigned long long *)&acc[(i64)pk * NL + j0 + q],
+                              (unsigned long long)(dg[q] * mult));
+        }
+        if (bad)
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    }
+}
+
+// Every vertex: its cluster, and fl(lambda_leave - birth) into that cluster's
+// accumulator.  Lanes of a warp with the same (cluster, digit position) add
+// their digits first (16-bit halves, so the 32-lane sums cannot overflow),
+// then one lane per group issues the atomics.
+__global__ void leaf_terms_kernel(i32 m, i32 n, const i32 *par, const i32 *jmp, const i32 *cid,
+                                  const float *w, const double *birth, u64 *acc, i32 *lcl,
+                                  FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const int lane = threadIdx.x & 31;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    for (i64 base = (blockIdx.x * (i64)blockDim.x + threadIdx.x) & ~(i64)31; base < n;
+         base += stride) {
+        const i64 x = base + lane;
+        u64 key = (1ull << 63) | (u64)lane;    // unique: contributes nothing
+        u32 dg[3] = {0, 0, 0};
+        int j0 = 0;
+        i32 k = 0;
+        bool bad = false;
+        if (x < n) {
+            const i32 a = jmp[m + x];
+            const i32 p = par[a];
+            k = cid[jmp[p]];
+            lcl[x] = k;
+            const double t = 1.0 / (double)w[p] - birth[k];
+            if (split_digits(t, j0, dg[0], dg[1], dg[2], bad))
+                key = ((u64)(u32)k << 4) | (u64)j0;
+        }
+        if (bad)
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+        const u32 grp = __match_any_sync(FULL, key);
+        u64 sum[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const u32 lo = __reduce_add_sync(grp, dg[q] & 0xFFFFu);
+            const u32 hi = __reduce_add_sync(grp, dg[q] >> 16);
+            sum[q] = (u64)lo + ((u64)hi << 16);
+        }
+        if (!(key >> 63) && lane == __ffs(grp) - 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (sum[q])
+                    atomicAdd((unsigned long long *)&acc[(i64)k * NL + j0 + q],
+                              (unsigned long long)sum[q]);
+        }
+    }
+}
+
+// Bits [pos, pos + cnt) (cnt <= 64) of the number held in 32-bit digits D.
+__host__ __device__ __forceinline__ u64 digit_bits(const u32 *D, int pos, int cnt)
+{
+    if (pos < 0 || cnt <= 0)
+        return 0;
+    const int i = pos >> 5, off = pos & 31;
+    auto dig = [&](int j) -> u64 { return j < NL ? (u64)D[j] : 0ull; };
+    const u64 lo = dig(i) | (dig(i + 1) << 32);
+    const u64 hi = dig(i + 2) | (dig(i + 3) << 32);
+    const u64 v = off ? (lo >> off) | (hi << (64 - off)) : lo;
+    return cnt == 64 ? v : v & ((1ull << cnt) - 1);
+}
+
+// The number held in NL 32-bit digits times 2^-FIX_EXP, rounded to the
+// nearest double (ties to even).
+__host__ __device__ __forceinline__ double round_fixed(const u32 *D)
+{
+    int top = -1;
+    for (int j = NL - 1; j >= 0; --j)
+        if (D[j]) {
+            top = 32 * j + 31 - leading_zeros(D[j]);
+            break;
+        }
+    if (top < 0)
+        return 0.0;
+    u64 mant;
+    int e2 = top - FIX_EXP;                        // value in [2^e2, 2^(e2+1))
+    if (top <= 52) {
+        mant = digit_bits(D, 0, top + 1) << (52 - top);
+    } else {
+        const int sh = top - 52;
+        mant = digit_bits(D, sh, 53);
+        const bool guard = digit_bits(D, sh - 1, 1) != 0;
+        bool sticky = false;
+        const int below = sh - 1;                  // bits [0, below) break ties
+        for (int j = 0; j < NL && 32 * j < below; ++j) {
+            const int hi_bit = below - 32 * j;
+            const u32 part = hi_bit >= 32 ? D[j] : (D[j] & ((1u << hi_bit) - 1));
+            if (part) {
+                sticky = true;
+                break;
+            }
+        }
+        if (guard && (sticky || (mant & 1))) {
+            ++mant;
+            if (mant == (1ull << 53)) {
+                mant >>= 1;
+                ++e2;
+            }
+        }
+    }
+    return bits_double(((u64)(e2 + 1023) << 52) | (mant & ((1ull << 52) - 1)));
+}
+
+// Carries between the 64-bit accumulator words, then round_fixed.
+__global__ void finalize_kernel(i32 K, const u64 *acc, double *stab, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        u32 D[NL];
+        u64 carry = 0;
+        for (int j = 0; j < NL; ++j) {
+            const u64 v = acc[k * NL + j] + carry;
+            D[j] = (u32)v;
+            carry = v >> 32;
+        }
+        if (carry) {
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+            continue;
+        }
+        stab[k] = round_fixed(D);
+    }
+}
+
+// ---- 5. excess of mass -----------------------------------------------------------
+__global__ void eom_kernel(i32 K, const i32 *cpar, const i32 *ckids, const i32 *ccnt,
+                           const double *stab, double *score, i32 *sel, i32 *arrive,
+                           const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root_cid = c->root_cid;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        if (k == root_cid || ccnt[k] != 0)
+            continue;
+        score[k] = stab[k];
+        sel[k] = 1;
+        i32 cur = (i32)k;
+        for (i32 it = 0; it < K; ++it) {
+            const i32 p = cpar[cur];
+            if (p < 0 || p == root_cid)
+                break;
+            __threadfence();
+            if (atomicAdd(&arrive[p], 1) == 0)
+                break;                             // the sibling continues
+            __threadfence();
+            const double s = __ldcg(&score[ckids[2 * (i64)p]]) +
+                             __ldcg(&score[ckids[2 * (i64)p + 1]]);
+            const double sp = stab[p];
+            const bool take = sp >= s;
+            sel[p] = take;
+            score[p] = take ? sp : s;
+            cur = p;
+        }
+    }
+}
+
+// ---- 6. labels --------------------------------------------------------------------
+__global__ void top_init_kernel(i32 K, const i32 *cpar, const i32 *sel, i32 *up, i32 *val,
+                                const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root_cid = c->root_cid;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 p = cpar[k];
+        up[k] = (k == root_cid || p == root_cid) ? -1 : p;
+        val[k] = (k != root_cid && sel[k]) ? (i32)k : -1;
+    }
+}
+
+// val: the topmost selected cluster among k and its 2^r nearest ancestors.
+__global__ void top_step_kernel(i32 K, const i32 *up, const i32 *val, i32 *up2, i32 *val2,
+                                const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 a = up[k];
+        if (a >= 0) {
+            const i32 va = val[a];
+            val2[k] = va >= 0 ? va : val[k];
+            up2[k] = up[a];
+        } else {
+            val2[k] = val[k];
+            up2[k] = -1;
+        }
+    }
+}
+
+__global__ void label_raw_kernel(i32 n, const i32 *lcl, const i32 *val, i32 *lab, i32 *first,
+                                 const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < n;
+         x += (i64)gridDim.x * blockDim.x) {
+        const i32 L = val[lcl[x]];
+        lab[x] = L;
+        if (L >= 0)
+            atomicMin(&first[L], (i32)x);
+    }
+}
+
+__global__ void first_flag_kernel(i32 n, const i32 *lab, const i32 *first, i32 *flag,
+                                  const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < n;
+         x += (i64)gridDim.x * blockDim.x) {
+        const i32 L = lab[x];
+        flag[x] = L >= 0 && first[L] == (i32)x;
+    }
+}
+
+__global__ void label_final_kernel(i32 n, const i32 *lab, const i32 *first, const i32 *rank,
+                                   const double *stab, i32 *labels, double *stab_out,
+                                   const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 x = blockIdx.x * (i64)blockDim.x + threadIdx.x; x < n;
+         x += (i64)gridDim.x * blockDim.x) {
+        const i32 L = lab[x];
+        if (L < 0) {
+            labels[x] = -1;
+            continue;
+        }
+        const i32 f = first[L];
+        const i32 r = rank[f];
+        labels[x] = r;
+        if (stab_out && f == (i32)x)
+            stab_out[r] = stab[L];
+    }
+}
+
+// ---- host side ------------------------------------------------------------------------
+int ceil_log2(i64 v)
+{
+    int r = 0;
+    while (((i64)1 << r) < v)
+        ++r;
+    return r;
+}
+
+struct Carve {
+    char *p;
+    size_t off = 0;
+    template <class T>
+    T *take(i64 count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *r = reinterpret_cast<T *>(p + off);
+        off += (size_t)(count > 0 ? count : 1) * sizeof(T);
+        return r;
+    }
+};
+
+struct FlatLayout {
+    FlatCtrl *ctrl;
+    i32 *par, *cnt, *kids, *size, *jmp, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
+    u64 *arcA, *arcB;
+    i32 *first, *cpar, *ckids, *ccnt, *csize, *arrive, *sel, *upA, *upB, *valA, *valB;
+    double *birth, *stab, *score;
+    u64 *acc;
+    size_t bytes;
+};
+
+FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
+{
+    const i64 m = n - 1, N = m + n, L = 2 * m + n;
+    const i64 nb = (N + SC_TILE - 1) / SC_TILE;
+    Carve cv{base};
+    FlatLayout l;
+    l.ctrl = cv.take<FlatCtrl>(1);
+    l.par = cv.take<i32>(N);
+    l.cnt = cv.take<i32>(m);
+    l.kids = cv.take<i32>(2 * m);
+    l.size = cv.take<i32>(m);
+    l.jmp = cv.take<i32>(N);
+    l.start = cv.take<i32>(m);
+    l.cid = cv.take<i32>(m);
+    l.bsum = cv.take<i32>(nb);
+    l.lcl = cv.take<i32>(n);
+    l.lab = cv.take<i32>(n);
+    l.flag = cv.take<i32>(n);
+    l.rank = cv.take<i32>(n);
+    l.arcA = cv.take<u64>(L);
+    l.arcB = cv.take<u64>(L);
+    l.first = cv.take<i32>(Kmax);
+    l.cpar = cv.take<i32>(Kmax);
+    l.ckids = cv.take<i32>(2 * Kmax);
+    l.ccnt = cv.take<i32>(Kmax);
+    l.csize = cv.take<i32>(Kmax);
+    l.arrive = cv.take<i32>(Kmax);
+    l.sel = cv.take<i32>(Kmax);
+    l.upA = cv.take<i32>(Kmax);
+    l.upB = cv.take<i32>(Kmax);
+    l.valA = cv.take<i32>(Kmax);
+    l.valB = cv.take<i32>(Kmax);
+    l.birth = cv.take<double>(Kmax);
+    l.stab = cv.take<double>(Kmax);
+    l.score = cv.take<double>(Kmax);
+    l.acc = cv.take<u64>(Kmax * NL);
+    l.bytes = cv.off + 256;
+    return l;
+}
+
+int grid_for(i64 count)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 148;
+    }
+    const i64 want = (count + FT - 1) / FT;
+    const i64 cap = (i64)sms * 8;
+    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+}
+
+void scan_flags(const i32 *in, i64 len, i32 *bsum, i32 *out, i32 *total, cudaStream_t s)
+{
+    const i64 nb = (len + SC_TILE - 1) / SC_TILE;
+    if (nb == 0)
+        return;
+    scan_reduce_kernel<<<(unsigned)nb, FT, 0, s>>>(in, len, bsum);
+    scan_top_kernel<<<1, 1024, 0, s>>>(bsum, nb, total);
+    scan_down_kernel<<<(unsigned)nb, FT, 0, s>>>(in, len, bsum, out);
+}
+
+// Launches every step on s; returns after reading the status.  The only
+// host synchronisation inside is the read of the cluster count.
+int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *w, i64 n,
+                i32 mcs, i64 Kmax, i32 *labels, double *stab_out, i64 *n_clusters,
+                cudaStream_t s)
+{
+    const i64 m = n - 1, N = m + n, L = 2 * m + n;
+    FlatCtrl *c = l.ctrl;
+    const i32 mi = (i32)m, ni = (i32)n;
+    cudaMemsetAsync(c, 0, sizeof(FlatCtrl), s);
+    cudaMemsetAsync(l.cnt, 0, sizeof(i32) * m, s);
+
+    // 1. parents and validation
+    flat_parents_kernel<<<grid_for(N), FT, 0, s>>>(ep, vp, w, mi, ni, l.par, l.cnt, l.kids, c);
+    flat_check_kernel<<<grid_for(m), FT, 0, s>>>(w, mi, l.par, l.cnt, c);
+    if (n >= mcs) {
+        // 2. leaf counts
+        tour_init_kernel<<<grid_for(L), FT, 0, s>>>(mi, ni, l.par, l.kids, l.arcA, c);
+        u64 *in = l.arcA, *out = l.arcB;
+        for (int r = ceil_log2(L); r > 0; --r) {
+            rank_step_kernel<<<grid_for(L), FT, 0, s>>>(in, out, L, c);
+            u64 *t = in;
+            in = out;
+            out = t;
+        }
+        sizes_kernel<<<grid_for(m), FT, 0, s>>>(in, mi, ni, l.size, c);
+        // 3. starts, anchors, cluster ids
+        anchor_init_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.kids, l.size, l.jmp,
+                                                      l.start, c);
+        for (int r = ceil_log2(N); r > 0; --r)
+            jump_kernel<<<grid_for(N), FT, 0, s>>>(l.jmp, N, c);
+        scan_flags(l.start, m, l.bsum, l.cid, &c->n_starts, s);
+        cudaMemsetAsync(l.ccnt, 0, sizeof(i32) * Kmax, s);
+        cudaMemsetAsync(l.arrive, 0, sizeof(i32) * Kmax, s);
+        cudaMemsetAsync(l.sel, 0, sizeof(i32) * Kmax, s);
+        cudaMemsetAsync(l.acc, 0, sizeof(u64) * Kmax * NL, s);
+        cudaMemsetAsync(l.first, 0x7F, sizeof(i32) * Kmax, s);
+        cluster_init_kernel<<<grid_for(m), FT, 0, s>>>(mi, Kmax, l.start, l.cid, l.par, l.jmp,
+                                                       l.size, w, l.cpar, l.ckids, l.ccnt,
+                                                       l.csize, l.birth, c);
+        FlatCtrl h{};
+        if (cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return PANDORA_ERR_CUDA;
+        if (h.status)
+            return h.status;
+        const i32 K = h.n_starts;
+        if (K < 1 || K > Kmax)
+            return PANDORA_ERR_NOT_A_DENDROGRAM;
+        // 4. stabilities
+        child_terms_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.csize, l.birth, l.acc, c);
+        leaf_terms_kernel<<<grid_for(n), FT, 0, s>>>(mi, ni, l.par, l.jmp, l.cid, w, l.birth,
+                                                     l.acc, l.lcl, c);
+        finalize_kernel<<<grid_for(K), FT, 0, s>>>(K, l.acc, l.stab, c);
+        // 5. excess of mass
+        eom_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.ckids, l.ccnt, l.stab, l.score, l.sel,
+                                              l.arrive, c);
+        // 6. labels
+        top_init_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.sel, l.upA, l.valA, c);
+        i32 *ua = l.upA, *va = l.valA, *ub = l.upB, *vb = l.valB;
+        for (int r = ceil_log2(K) + 1; r > 0; --r) {
+            top_step_kernel<<<grid_for(K), FT, 0, s>>>(K, ua, va, ub, vb, c);
+            i32 *t = ua;
+            ua = ub;
+            ub = t;
+            t = va;
+            va = vb;
+            vb = t;
+        }
+        label_raw_kernel<<<grid_for(n), FT, 0, s>>>(ni, l.lcl, va, l.lab, l.first, c);
+        first_flag_kernel<<<grid_for(n), FT, 0, s>>>(ni, l.lab, l.first, l.flag, c);
+        scan_flags(l.flag, n, l.bsum, l.rank, &c->n_selected, s);
+        label_final_kernel<<<grid_for(n), FT, 0, s>>>(ni, l.lab, l.first, l.rank, l.stab, labels,
+                                                      stab_out, c);
+    } else {
+        cudaMemsetAsync(labels, 0xFF, sizeof(i32) * n, s);   // too few points: all noise
+    }
+    if (cudaGetLastError() != cudaSuccess)
+        return PANDORA_ERR_CUDA;
+    FlatCtrl h{};
+    if (cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PANDORA_ERR_CUDA;
+    if (h.status)
+        return h.status;
+    if (n_clusters)
+        *n_clusters = n >= mcs ? h.n_selected : 0;
+    return PANDORA_OK;
+}
+
+int run_flat(const i32 *ep, const i32 *vp, const float *w, i64 n, i32 mcs, i32 *labels,
+             double *stab_out, i64 *n_clusters, cudaStream_t s)
+{
+    const i64 Kmax = 2 * (n / mcs) + 1;
+    const size_t bytes = flat_layout(nullptr, n, Kmax).bytes;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return PANDORA_ERR_CUDA;
+    cudaMemPool_t pool = flat_pool(dev);
+    if (!pool)
+        return PANDORA_ERR_CUDA;
+    void *ws = nullptr;
+    if (cudaMallocFromPoolAsync(&ws, bytes, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PANDORA_ERR_OUT_OF_MEMORY;
+    }
+    const int st = run_flat_on(flat_layout((char *)ws, n, Kmax), ep, vp, w, n, mcs, Kmax,
+                               labels, stab_out, n_clusters, s);
+    cudaFreeAsync(ws, s);
+    if (st != PANDORA_OK)
+        cudaStreamSynchronize(s);
+    return st;
+}
+
+}  // namespace
+
+extern "C" int pandora_hdbscan_labels(const int32_t *edge_parent, const int32_t *vertex_parent,
+                                      const float *w, int64_t n_vertices,
+                                      int32_t min_cluster_size, int32_t *labels,
+                                      double *cluster_stability, int64_t *n_clusters,
+                                      void *stream)
+{
+    if (n_vertices < 0 || min_cluster_size < 2)
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (n_vertices > PANDORA_FLAT_MAX_VERTICES)
+        return PANDORA_ERR_SIZE_LIMIT;
+    if (n_vertices > 0 && (!labels || !vertex_parent))
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    if (n_vertices > 1 && (!edge_parent || !w))
+        return PANDORA_ERR_INVALID_ARGUMENT;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_vertices <= 1) {
+        if (n_vertices == 1 && cudaMemsetAsync(labels, 0xFF, sizeof(int32_t), s) != cudaSuccess)
+            return PANDORA_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess)
+            return PANDORA_ERR_CUDA;
+        if (n_clusters)
+            *n_clusters = 0;
+        return PANDORA_OK;
+    }
+    return run_flat(edge_parent, vertex_parent, w, n_vertices, min_cluster_size, labels,
+                    cluster_stability, n_clusters, s);
+}

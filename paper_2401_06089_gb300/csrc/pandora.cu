@@ -1069,6 +1069,9 @@ int run_on_workspace(const i32 *u, const i32 *v, const float *w, i64 M, i32 *ep,
 
 size_t workspace_bytes(i64 M, i64 T) { return total_workspace(M, T); }
 
+// The library's stream-ordered pool of `dev`, for the flat-cluster entry point.
+cudaMemPool_t flat_pool(int dev) { return library_pool(dev); }
+
 }  // namespace pandora
 
 using namespace pandora;
@@ -1271,7 +1274,9 @@ const char *pandora_status_string(int status)
     case PANDORA_ERR_OUT_OF_MEMORY: return "out of device memory";
     case PANDORA_ERR_CUDA: return "CUDA runtime error";
     case PANDORA_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
-    case PANDORA_ERR_SIZE_LIMIT: return "input larger than the static scratch of pandora_dendrogram_noalloc";
+    case PANDORA_ERR_SIZE_LIMIT: return "input above the entry point's size limit";
+    case PANDORA_ERR_BAD_WEIGHT: return "weight not positive and finite";
+    case PANDORA_ERR_NOT_A_DENDROGRAM: return "parent arrays are not a weight-ordered binary dendrogram";
     default: return "unknown status";
     }
 }

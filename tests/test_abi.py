@@ -65,6 +65,16 @@ def test_argument_errors_are_reported_before_any_launch(lib):
     assert bl.pandora_dendrogram_batched(null, null, null, null, 3, 10, null, null, null) == 1
     sz = ctypes.c_size_t(0)
     assert bl.pandora_workspace_size(10, 0, ctypes.byref(sz)) == 1
+    # flat clusters: min_cluster_size below 2, negative size, null arrays,
+    # above the size limit
+    nc = ctypes.c_int64(-5)
+    flat = bl.pandora_hdbscan_labels
+    assert flat(null, null, null, 10, 1, null, null, ctypes.byref(nc), null) == 1
+    assert flat(null, null, null, -1, 2, null, null, ctypes.byref(nc), null) == 1
+    assert flat(null, null, null, 10, 2, null, null, ctypes.byref(nc), null) == 1
+    assert flat(null, null, null, _binding.FLAT_MAX_VERTICES + 1, 2, null, null,
+                ctypes.byref(nc), null) == 10
+    assert nc.value == -5
 
 
 def test_noalloc_scratch_holds_the_largest_accepted_input():
