@@ -315,10 +315,10 @@ int pandora_profile_read(pandora_profile *out);
  * that fall off in smaller parts.  Its stability is the sum over its points
  * of (lambda at which the point leaves it - lambda at its birth), each term
  * in float64, summed exactly and rounded once (so the value does not depend
- * on any order).  Excess of mass: over all clusters but the whole tree, from
- * the leaves of the cluster tree up, a cluster is kept instead of the best
- * set found under it when its stability is at least that set's total (the
- * total of two float64 values, rounded once).
+ * on any order).  Excess of mass: over all clusters but the whole tree, the
+ * set of non-nested clusters of largest total stability, totals taken
+ * exactly; a cluster is kept instead of the best set under it when its
+ * stability is at least that set's total (a parent wins a tie).
  *
  * Output: labels[n_vertices] (device): the kept cluster that contains the
  * point, numbered 0, 1, ... in increasing order of each cluster's smallest

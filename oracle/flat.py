@@ -29,9 +29,11 @@ mass").  Written out:
 * selection, children before parents, over every cluster but the root (the
   whole data set is not a candidate): a cluster with no child cluster is
   selected and scores its stability; otherwise its children's scores are
-  summed (exactly, rounded once) and the cluster is selected, and its
-  descendants deselected, when its stability is at least that sum (so a
-  parent wins a tie), scoring its stability, else it scores the sum;
+  summed exactly (no rounding: a score is an exact sum of float64
+  stabilities, so the selection is the exact optimum of the total
+  stability) and the cluster is selected, and its descendants deselected,
+  when its stability is at least that sum (so a parent wins a tie), scoring
+  its stability, else it scores the sum;
 * label of a vertex: the selected cluster among the cluster it leaves and that
   cluster's ancestors, or -1 (noise); selected clusters are numbered 0, 1, ...
   in increasing order of their smallest vertex id.
@@ -52,8 +54,8 @@ def hdbscan_labels(edge_parent, vertex_parent, w, min_cluster_size, members: boo
     """Returns (labels int32[n], info) for a dendrogram of m edges and
     n = m + 1 vertices.  info["clusters"]: per cluster (in creation order,
     cluster 0 the root) its starting node ("e", edge) or the root edge, parent
-    cluster, birth lambda, size, stability, score, selection and label (-1
-    unless selected); with
+    cluster, birth lambda, size, stability, score (exact, a Fraction),
+    selection and label (-1 unless selected); with
     ``members`` also its sorted vertex ids."""
     ep = np.asarray(edge_parent, dtype=np.int64)
     vp = np.asarray(vertex_parent, dtype=np.int64)
@@ -145,17 +147,17 @@ def hdbscan_labels(edge_parent, vertex_parent, w, min_cluster_size, members: boo
     # excess of mass, children before parents (creation order is top-down);
     # the root cluster is not a candidate
     selected = [False] * len(clusters)
-    score = [0.0] * len(clusters)
+    score = [Fraction(0)] * len(clusters)
     for ci in range(len(clusters) - 1, 0, -1):
         C = clusters[ci]
         if not C["children"]:
             selected[ci] = True
-            score[ci] = C["stability"]
+            score[ci] = Fraction(C["stability"])
             continue
-        tot = _round(sum((Fraction(score[di]) for di in C["children"]), Fraction(0)))
-        if C["stability"] >= tot:
+        tot = sum((score[di] for di in C["children"]), Fraction(0))
+        if Fraction(C["stability"]) >= tot:
             selected[ci] = True
-            score[ci] = C["stability"]
+            score[ci] = Fraction(C["stability"])
             st = list(C["children"])
             while st:
                 d = st.pop()

@@ -15,7 +15,7 @@
 //  1. parents, child slots and validation (binary tree, one root, every
 //     parent later than its child in (weight, index) order, weights > 0);
 //  2. leaf counts: Euler tour of the dendrogram (down/up arc per edge, one
-//     arc per leaf), suffix sums by Wyllie pointer jumping;
+//     arc per leaf), suffix sums by list ranking over a sparse ruling set;
 //  3. per node: big = leaf count >= mcs; cluster starts (the root, and both
 //     children of an edge whose children are both big); anchors (starts, and
 //     small nodes under a big parent); nearest anchor above every node by
@@ -29,9 +29,9 @@
 //     of 32-bit digits with integer atomics; the exact sum is rounded once to
 //     float64 (round to nearest, ties to even).  The result does not depend on
 //     the order of the additions;
-//  5. excess of mass bottom-up over the binary cluster tree: the second child
-//     to finish continues with the parent (an atomic arrival count; nothing
-//     waits);
+//  5. excess of mass over the binary cluster tree, exactly (children's best
+//     totals are exact sums of float64 stabilities), by parallel tree
+//     contraction (rake rounds, then the rakes replayed in reverse);
 //  6. labels: the topmost selected cluster above a vertex's cluster (pointer
 //     jumping over the cluster tree), numbered by smallest member (two scans).
 #include <cfloat>
@@ -60,7 +60,8 @@ struct FlatCtrl {
     int n_starts;      // clusters (start edges), from the scan
     int root_cid;      // cluster id of the root
     int n_selected;    // selected clusters, from the scan
-    int pad[2];
+    int n_leaves;      // leaf clusters, from the scan
+    u32 rs_count;      // splitters of the list ranking
 };
 
 __device__ __forceinline__ bool failed(const FlatCtrl *c)
@@ -175,6 +176,95 @@ __global__ void rank_step_kernel(const u64 *in, u64 *out, i64 L, const FlatCtrl 
         } else {
             out[a] = r;
         }
+    }
+}
+
+// Suffix sums by a sparse ruling set: about one arc in 64 (by a hash of its
+// id, plus the head and the root's unused up arc) is a splitter; one thread
+// per splitter walks its segment up to the next splitter, recording for every
+// arc its segment and the sum before it; the short list of segments is
+// ranked by pointer jumping; then suffix(a) = suffix(segment) - (sum before a).
+// O(L) work instead of the O(L log L) of jumping on the whole list.
+constexpr u32 RS_MASK = 63;
+
+__device__ __forceinline__ bool rs_splitter(i64 a, i64 head)
+{
+    u32 h = (u32)a * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    return a == head || a == head + 1 || (h & RS_MASK) == 0;
+}
+
+inline i64 rs_capacity(i64 L) { return L / 48 + 4096; }
+
+__global__ void rs_pick_kernel(i64 L, i32 *sid_of, i32 *spl, i64 cap, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i64 head = 2 * (i64)c->root;
+    for (i64 a = blockIdx.x * (i64)blockDim.x + threadIdx.x; a < L;
+         a += (i64)gridDim.x * blockDim.x) {
+        if (!rs_splitter(a, head))
+            continue;
+        const u32 id = atomicAdd(&c->rs_count, 1u);
+        if ((i64)id < cap) {
+            spl[id] = (i32)a;
+            sid_of[a] = (i32)id;
+        } else {
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+        }
+    }
+}
+
+// seg[i]: next segment (high 32 bits, -1 at the end) | sum of the segment.
+__global__ void rs_walk_kernel(const u64 *arc, u64 *owner_loc, const i32 *sid_of, const i32 *spl,
+                               i64 cap, i64 L, u64 *seg, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i64 head = 2 * (i64)c->root;
+    const i64 cnt = (i64)c->rs_count < cap ? (i64)c->rs_count : cap;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < cnt;
+         i += (i64)gridDim.x * blockDim.x) {
+        i64 a = spl[i];
+        u32 sum = 0;
+        u32 next_seg = 0xFFFFFFFFu;
+        for (i64 steps = 0;; ++steps) {
+            if (steps > L) {
+                set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+                break;
+            }
+            const u64 w = arc[a];
+            owner_loc[a] = ((u64)i << 32) | sum;
+            sum += (u32)w;
+            const i32 nx = (i32)(w >> 32);
+            if (nx < 0)
+                break;
+            if (rs_splitter(nx, head)) {
+                next_seg = (u32)sid_of[nx];
+                break;
+            }
+            a = nx;
+        }
+        seg[i] = ((u64)next_seg << 32) | sum;
+    }
+}
+
+__global__ void rs_final_kernel(const u64 *owner_loc, const u64 *seg_suf, i64 cap, i64 L,
+                                u64 *suf, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 a = blockIdx.x * (i64)blockDim.x + threadIdx.x; a < L;
+         a += (i64)gridDim.x * blockDim.x) {
+        const u64 ol = owner_loc[a];
+        const i64 own = (i64)(ol >> 32);
+        if (own >= cap) {
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+            continue;
+        }
+        suf[a] = (u32)seg_suf[own] - (u32)ol;
     }
 }
 
@@ -397,7 +487,7 @@ __host__ __device__ __forceinline__ bool split_digits(double t, int &j0, u32 &d0
 __global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32 *cid,
                                     const i32 *par, const i32 *jmp, const i32 *size,
                                     const float *w, i32 *cpar, i32 *ckids, i32 *ccnt, i32 *csize,
-                                    double *birth, FlatCtrl *c)
+                                    i32 *cedge, double *birth, FlatCtrl *c)
 {
     if (failed(c))
         return;
@@ -413,6 +503,7 @@ __global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32
             continue;
         }
         csize[k] = size[e];
+        cedge[k] = (i32)e;
         if (e == root) {
             cpar[k] = -1;
             birth[k] = 0.0;
@@ -582,36 +673,251 @@ __global__ void finalize_kernel(i32 K, const u64 *acc, double *stab, FlatCtrl *c
 }
 
 // ---- 5. excess of mass -----------------------------------------------------------
-__global__ void eom_kernel(i32 K, const i32 *cpar, const i32 *ckids, const i32 *ccnt,
-                           const double *stab, double *score, i32 *sel, i32 *arrive,
-                           const FlatCtrl *c)
+// best(C) = max(stab(C), best(D1) + best(D2)) over the binary cluster tree,
+// with exact sums (448-bit fixed point, unit 2^-FIX_EXP: stabilities are
+// float64 multiples of 2^-180 below 2^213, and sums of at most 2^30 of them
+// stay below 2^243).  The tree can be as deep as it is large (a caterpillar
+// shedding one small cluster per level), so it is contracted in O(log K)
+// rounds: leaves are numbered left to right in the dendrogram's tour order
+// (the first and last leaf left out), and each round rakes the odd-numbered
+// leaves that are left children, then those that are right children, then
+// halves the numbers -- the classical schedule under which no two
+// simultaneous rakes touch the same nodes.  Raking leaf l removes l and its
+// parent p and hangs l's sibling s from p's parent; the edge above s carries
+// f(x) = max(a, x + b) (a may be -inf), and such functions compose exactly:
+//     f_s <- f_p o (x -> max(stab(p), k + f_s(x))),   k = f_l(best(l)).
+// Replaying the rakes in reverse then gives every best(p) =
+// max(stab(p), k + f_s(best(s))) from values already known.
+struct __align__(8) Big {
+    u32 d[NL];
+};
+
+__device__ __forceinline__ Big big_add(const Big &a, const Big &b)
+{
+    Big r;
+    u64 c = 0;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        const u64 t = (u64)a.d[j] + b.d[j] + c;
+        r.d[j] = (u32)t;
+        c = t >> 32;
+    }
+    return r;
+}
+
+__device__ __forceinline__ bool big_less(const Big &a, const Big &b)
+{
+#pragma unroll
+    for (int j = NL - 1; j >= 0; --j)
+        if (a.d[j] != b.d[j])
+            return a.d[j] < b.d[j];
+    return false;
+}
+
+__device__ __forceinline__ Big big_from_double(double t, bool &bad)
+{
+    Big r;
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+        r.d[j] = 0;
+    int j0;
+    u32 d0, d1, d2;
+    if (split_digits(t, j0, d0, d1, d2, bad)) {
+        r.d[j0] = d0;
+        r.d[j0 + 1] = d1;
+        r.d[j0 + 2] = d2;
+    }
+    return r;
+}
+
+// Per-cluster arrays of the contraction.
+struct Eom {
+    i32 *cur_par, *cur_kid, *leafnum, *rake_step, *rk_s, *a_inf, *rk_as_inf;
+    Big *a, *b, *bstab, *best, *rk_k, *rk_as, *rk_bs;
+};
+
+constexpr i32 LEAF_INTERNAL = -1, LEAF_RAKED = -2;
+
+// Orientation of the children (left = first in the tour, i.e. the larger
+// suffix leaf count), identity edge functions, exact stabilities, and a flag
+// at every leaf cluster's tour position (number of leaves before it).
+__global__ void eom_prep_kernel(i32 K, i32 n, const i32 *cedge, const u64 *suf, const i32 *ckids,
+                                const i32 *ccnt, const i32 *cpar, const double *stab, Eom E,
+                                i32 *posflag, FlatCtrl *c)
 {
     if (failed(c))
         return;
     const i32 root_cid = c->root_cid;
     for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
          k += (i64)gridDim.x * blockDim.x) {
-        if (k == root_cid || ccnt[k] != 0)
-            continue;
-        score[k] = stab[k];
-        sel[k] = 1;
-        i32 cur = (i32)k;
-        for (i32 it = 0; it < K; ++it) {
-            const i32 p = cpar[cur];
-            if (p < 0 || p == root_cid)
-                break;
-            __threadfence();
-            if (atomicAdd(&arrive[p], 1) == 0)
-                break;                             // the sibling continues
-            __threadfence();
-            const double s = __ldcg(&score[ckids[2 * (i64)p]]) +
-                             __ldcg(&score[ckids[2 * (i64)p + 1]]);
-            const double sp = stab[p];
-            const bool take = sp >= s;
-            sel[p] = take;
-            score[p] = take ? sp : s;
-            cur = p;
+        bool bad = false;
+        const Big bs = big_from_double(stab[k], bad);
+        if (bad)
+            set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+        E.bstab[k] = bs;
+        E.cur_par[k] = cpar[k];
+        E.a_inf[k] = 1;
+        Big z;
+#pragma unroll
+        for (int j = 0; j < NL; ++j)
+            z.d[j] = 0;
+        E.b[k] = z;
+        E.rake_step[k] = -1;
+        if (ccnt[k] == 2) {
+            i32 x = ckids[2 * k], y = ckids[2 * k + 1];
+            if ((u32)suf[2 * (i64)cedge[x]] < (u32)suf[2 * (i64)cedge[y]]) {
+                const i32 t = x;
+                x = y;
+                y = t;
+            }
+            E.cur_kid[2 * k] = x;
+            E.cur_kid[2 * k + 1] = y;
+            E.leafnum[k] = LEAF_INTERNAL;
+        } else {
+            E.leafnum[k] = 0;
+            E.best[k] = bs;
+            if (k != root_cid)
+                posflag[n - (u32)suf[2 * (i64)cedge[k]]] = 1;
         }
+    }
+}
+
+// Leaves get their left-to-right rank; the first and the last stay 0.
+__global__ void eom_number_kernel(i32 K, i32 n, i32 n_leaves, const i32 *cedge, const u64 *suf,
+                                  const i32 *rank, Eom E, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c->n_leaves != n_leaves)
+        set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        if (E.leafnum[k] != 0 || k == c->root_cid)
+            continue;
+        const i32 r = rank[n - (u32)suf[2 * (i64)cedge[k]]];
+        E.leafnum[k] = (r >= 1 && r <= n_leaves - 2) ? r : 0;
+    }
+}
+
+__global__ void rake_kernel(i32 K, int side, i32 step, Eom E, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 l = blockIdx.x * (i64)blockDim.x + threadIdx.x; l < K;
+         l += (i64)gridDim.x * blockDim.x) {
+        const i32 num = E.leafnum[l];
+        if (num <= 0 || !(num & 1))
+            continue;
+        const i32 p = E.cur_par[l];
+        const int sd = E.cur_kid[2 * (i64)p] == (i32)l ? 0 : 1;
+        if (sd != side)
+            continue;
+        const i32 sb = E.cur_kid[2 * (i64)p + 1 - sd];
+        const i32 g = E.cur_par[p];
+        if (g < 0) {                               // never under this schedule
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+            continue;
+        }
+        // k = f_l(best(l)); l is a leaf of the original tree, best = stab
+        Big kv = big_add(E.bstab[l], E.b[l]);
+        if (!E.a_inf[l] && big_less(kv, E.a[l]))
+            kv = E.a[l];
+        const int as_inf = E.a_inf[sb];
+        const Big as = E.a[sb], bs = E.b[sb];
+        E.rk_s[p] = sb;
+        E.rk_k[p] = kv;
+        E.rk_as_inf[p] = as_inf;
+        E.rk_as[p] = as;
+        E.rk_bs[p] = bs;
+        E.rake_step[p] = step;
+        // h(x) = max(A, x + B): A = max(stab(p), k + a_s), B = k + b_s
+        Big A = E.bstab[p];
+        if (!as_inf) {
+            const Big t = big_add(kv, as);
+            if (big_less(A, t))
+                A = t;
+        }
+        const Big Bv = big_add(kv, bs);
+        // f_p o h = max(max(a_p, A + b_p), x + B + b_p)
+        const Big bp = E.b[p];
+        Big a2 = big_add(A, bp);
+        if (!E.a_inf[p] && big_less(a2, E.a[p]))
+            a2 = E.a[p];
+        E.a[sb] = a2;
+        E.a_inf[sb] = 0;
+        E.b[sb] = big_add(Bv, bp);
+        E.cur_par[sb] = g;
+        const int gs = E.cur_kid[2 * (i64)g] == p ? 0 : 1;
+        E.cur_kid[2 * (i64)g + gs] = sb;
+        E.leafnum[l] = LEAF_RAKED;
+    }
+}
+
+__global__ void renumber_kernel(i32 K, Eom E, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        const i32 num = E.leafnum[k];
+        if (num <= 0)
+            continue;
+        if (num & 1)                               // an odd leaf that was not raked
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+        else
+            E.leafnum[k] = num >> 1;
+    }
+}
+
+// Every internal cluster but the root must have been raked.
+__global__ void rake_check_kernel(i32 K, Eom E, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x)
+        if (E.leafnum[k] == LEAF_INTERNAL && k != c->root_cid && E.rake_step[k] < 0)
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+}
+
+__global__ void expand_step_kernel(i32 K, i32 step, Eom E, const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 p = blockIdx.x * (i64)blockDim.x + threadIdx.x; p < K;
+         p += (i64)gridDim.x * blockDim.x) {
+        if (E.rake_step[p] != step)
+            continue;
+        Big v = big_add(E.best[E.rk_s[p]], E.rk_bs[p]);   // f_s(best(s)) at rake time
+        if (!E.rk_as_inf[p] && big_less(v, E.rk_as[p]))
+            v = E.rk_as[p];
+        Big t = big_add(E.rk_k[p], v);
+        if (big_less(t, E.bstab[p]))
+            t = E.bstab[p];
+        E.best[p] = t;
+    }
+}
+
+// Keep C (for now) when stab(C) >= best(D1) + best(D2), exactly; a cluster
+// without children is kept; the root is not a candidate.
+__global__ void decide_kernel(i32 K, const i32 *ckids, const i32 *ccnt, Eom E, i32 *sel,
+                              const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i32 root_cid = c->root_cid;
+    for (i64 k = blockIdx.x * (i64)blockDim.x + threadIdx.x; k < K;
+         k += (i64)gridDim.x * blockDim.x) {
+        if (k == root_cid) {
+            sel[k] = 0;
+            continue;
+        }
+        if (ccnt[k] == 0) {
+            sel[k] = 1;
+            continue;
+        }
+        const Big kids = big_add(E.best[ckids[2 * k]], E.best[ckids[2 * k + 1]]);
+        sel[k] = !big_less(E.bstab[k], kids);
     }
 }
 
@@ -722,10 +1028,14 @@ struct Carve {
 struct FlatLayout {
     FlatCtrl *ctrl;
     i32 *par, *cnt, *kids, *size, *jmp, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
-    u64 *arcA, *arcB;
-    i32 *first, *cpar, *ckids, *ccnt, *csize, *arrive, *sel, *upA, *upB, *valA, *valB;
-    double *birth, *stab, *score;
+    u64 *arcA, *arcB;       // tour words, then suffix sums (A); segment owner and offset (B)
+    i32 *sid_of, *spl;      // ruling set: splitter id per arc, splitter arcs
+    u64 *segA, *segB;       // ruling set: segment words
+    i64 rs_cap;
+    i32 *first, *cpar, *ckids, *ccnt, *csize, *cedge, *sel, *upA, *upB, *valA, *valB;
+    double *birth, *stab;
     u64 *acc;
+    Eom eom;
     size_t bytes;
 };
 
@@ -750,12 +1060,17 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.rank = cv.take<i32>(n);
     l.arcA = cv.take<u64>(L);
     l.arcB = cv.take<u64>(L);
+    l.rs_cap = rs_capacity(L);
+    l.sid_of = cv.take<i32>(L);
+    l.spl = cv.take<i32>(l.rs_cap);
+    l.segA = cv.take<u64>(l.rs_cap);
+    l.segB = cv.take<u64>(l.rs_cap);
     l.first = cv.take<i32>(Kmax);
     l.cpar = cv.take<i32>(Kmax);
     l.ckids = cv.take<i32>(2 * Kmax);
     l.ccnt = cv.take<i32>(Kmax);
     l.csize = cv.take<i32>(Kmax);
-    l.arrive = cv.take<i32>(Kmax);
+    l.cedge = cv.take<i32>(Kmax);
     l.sel = cv.take<i32>(Kmax);
     l.upA = cv.take<i32>(Kmax);
     l.upB = cv.take<i32>(Kmax);
@@ -763,8 +1078,22 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.valB = cv.take<i32>(Kmax);
     l.birth = cv.take<double>(Kmax);
     l.stab = cv.take<double>(Kmax);
-    l.score = cv.take<double>(Kmax);
     l.acc = cv.take<u64>(Kmax * NL);
+    Eom &E = l.eom;
+    E.cur_par = cv.take<i32>(Kmax);
+    E.cur_kid = cv.take<i32>(2 * Kmax);
+    E.leafnum = cv.take<i32>(Kmax);
+    E.rake_step = cv.take<i32>(Kmax);
+    E.rk_s = cv.take<i32>(Kmax);
+    E.a_inf = cv.take<i32>(Kmax);
+    E.rk_as_inf = cv.take<i32>(Kmax);
+    E.a = cv.take<Big>(Kmax);
+    E.b = cv.take<Big>(Kmax);
+    E.bstab = cv.take<Big>(Kmax);
+    E.best = cv.take<Big>(Kmax);
+    E.rk_k = cv.take<Big>(Kmax);
+    E.rk_as = cv.take<Big>(Kmax);
+    E.rk_bs = cv.take<Big>(Kmax);
     l.bytes = cv.off + 256;
     return l;
 }
@@ -812,14 +1141,20 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
     if (n >= mcs) {
         // 2. leaf counts
         tour_init_kernel<<<grid_for(L), FT, 0, s>>>(mi, ni, l.par, l.kids, l.arcA, c);
-        u64 *in = l.arcA, *out = l.arcB;
-        for (int r = ceil_log2(L); r > 0; --r) {
-            rank_step_kernel<<<grid_for(L), FT, 0, s>>>(in, out, L, c);
+        cudaMemsetAsync(l.segA, 0xFF, sizeof(u64) * l.rs_cap, s);   // unused: next = -1
+        rs_pick_kernel<<<grid_for(L), FT, 0, s>>>(L, l.sid_of, l.spl, l.rs_cap, c);
+        rs_walk_kernel<<<grid_for(l.rs_cap), FT, 0, s>>>(l.arcA, l.arcB, l.sid_of, l.spl,
+                                                         l.rs_cap, L, l.segA, c);
+        u64 *in = l.segA, *out = l.segB;
+        for (int r = ceil_log2(l.rs_cap); r > 0; --r) {
+            rank_step_kernel<<<grid_for(l.rs_cap), FT, 0, s>>>(in, out, l.rs_cap, c);
             u64 *t = in;
             in = out;
             out = t;
         }
-        sizes_kernel<<<grid_for(m), FT, 0, s>>>(in, mi, ni, l.size, c);
+        rs_final_kernel<<<grid_for(L), FT, 0, s>>>(l.arcB, in, l.rs_cap, L, l.arcA, c);
+        const u64 *suf = l.arcA;
+        sizes_kernel<<<grid_for(m), FT, 0, s>>>(suf, mi, ni, l.size, c);
         // 3. starts, anchors, cluster ids
         anchor_init_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.kids, l.size, l.jmp,
                                                       l.start, c);
@@ -827,13 +1162,12 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
             jump_kernel<<<grid_for(N), FT, 0, s>>>(l.jmp, N, c);
         scan_flags(l.start, m, l.bsum, l.cid, &c->n_starts, s);
         cudaMemsetAsync(l.ccnt, 0, sizeof(i32) * Kmax, s);
-        cudaMemsetAsync(l.arrive, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.sel, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.acc, 0, sizeof(u64) * Kmax * NL, s);
         cudaMemsetAsync(l.first, 0x7F, sizeof(i32) * Kmax, s);
         cluster_init_kernel<<<grid_for(m), FT, 0, s>>>(mi, Kmax, l.start, l.cid, l.par, l.jmp,
                                                        l.size, w, l.cpar, l.ckids, l.ccnt,
-                                                       l.csize, l.birth, c);
+                                                       l.csize, l.cedge, l.birth, c);
         FlatCtrl h{};
         if (cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
@@ -848,9 +1182,27 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
         leaf_terms_kernel<<<grid_for(n), FT, 0, s>>>(mi, ni, l.par, l.jmp, l.cid, w, l.birth,
                                                      l.acc, l.lcl, c);
         finalize_kernel<<<grid_for(K), FT, 0, s>>>(K, l.acc, l.stab, c);
-        // 5. excess of mass
-        eom_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.ckids, l.ccnt, l.stab, l.score, l.sel,
-                                              l.arrive, c);
+        // 5. excess of mass (K == 1: no candidate, nothing kept)
+        if (K >= 3) {
+            const Eom &E = l.eom;
+            const i32 n_leaves = (K + 1) / 2;
+            cudaMemsetAsync(l.flag, 0, sizeof(i32) * n, s);
+            eom_prep_kernel<<<grid_for(K), FT, 0, s>>>(K, ni, l.cedge, suf, l.ckids, l.ccnt,
+                                                       l.cpar, l.stab, E, l.flag, c);
+            scan_flags(l.flag, n, l.bsum, l.rank, &c->n_leaves, s);
+            eom_number_kernel<<<grid_for(K), FT, 0, s>>>(K, ni, n_leaves, l.cedge, suf, l.rank,
+                                                         E, c);
+            const int rounds = ceil_log2(n_leaves) + 1;
+            for (int r = 0; r < rounds; ++r) {
+                rake_kernel<<<grid_for(K), FT, 0, s>>>(K, 0, 2 * r, E, c);
+                rake_kernel<<<grid_for(K), FT, 0, s>>>(K, 1, 2 * r + 1, E, c);
+                renumber_kernel<<<grid_for(K), FT, 0, s>>>(K, E, c);
+            }
+            rake_check_kernel<<<grid_for(K), FT, 0, s>>>(K, E, c);
+            for (int t = 2 * rounds - 1; t >= 0; --t)
+                expand_step_kernel<<<grid_for(K), FT, 0, s>>>(K, t, E, c);
+            decide_kernel<<<grid_for(K), FT, 0, s>>>(K, l.ckids, l.ccnt, E, l.sel, c);
+        }
         // 6. labels
         top_init_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.sel, l.upA, l.valA, c);
         i32 *ua = l.upA, *va = l.valA, *ub = l.upB, *vb = l.valB;
