@@ -69,6 +69,9 @@ def parse_args():
                     help="compare the outputs with the oracle after the timed region")
     ap.add_argument("--async-api", action="store_true",
                     help="time pandora_dendrogram_async (worst-case level count, no host sync)")
+    ap.add_argument("--flat", type=int, default=0, metavar="MCS",
+                    help="also time HDBSCAN* flat clusters (pandora_hdbscan_labels) with this "
+                         "min_cluster_size on the workload's dendrogram")
     return ap.parse_args()
 
 
@@ -802,6 +805,26 @@ def main():
         line["cpu_baseline"] = {"value": ts.m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{spec['family']} n={n_s} seed={spec['seed']}, "
                                           f"one thread, {sec:.1f} s"}
+    # ---- HDBSCAN* flat clusters on the same dendrogram (optional) ----------
+    if args.flat and rank == 0:
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        for _ in range(max(args.warmup, 3)):
+            labels = pd.hdbscan_labels(ep, vp, w, args.flat)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        k3 = max(3, args.steps // 2)
+        a.record(stream)
+        for _ in range(k3):
+            labels = pd.hdbscan_labels(ep, vp, w, args.flat)
+        b.record(stream)
+        b.synchronize()
+        ms3 = a.elapsed_time(b) / k3
+        lab_np = labels.cpu().numpy()
+        line["flat_clusters"] = {"min_cluster_size": args.flat, "ms_per_call": ms3,
+                                 "points_per_s": (m + 1) / (ms3 / 1e3), "steps": k3,
+                                 "clusters": int(lab_np.max()) + 1,
+                                 "noise_fraction": float((lab_np < 0).mean())}
     if args.check and rank == 0:
         import oracle
         oracle.build()

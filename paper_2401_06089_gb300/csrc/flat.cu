@@ -62,11 +62,30 @@ struct FlatCtrl {
     int n_selected;    // selected clusters, from the scan
     int n_leaves;      // leaf clusters, from the scan
     u32 rs_count;      // splitters of the list ranking
+    u32 bp_count;      // splitters of the path heads
+    u32 unresolved;    // segments still without their start (per round)
 };
 
 __device__ __forceinline__ bool failed(const FlatCtrl *c)
 {
     return *(const volatile int *)&c->status != 0;
+}
+
+// Slot in a list appended to by many threads: one atomic per warp on the
+// shared counter (a counter hit by every thread serialises in L2).
+__device__ __forceinline__ u32 warp_append(u32 *counter, bool want)
+{
+    const u32 active = __activemask();
+    const u32 mask = __ballot_sync(active, want);
+    if (!want)
+        return 0;
+    const int leader = __ffs(mask) - 1;
+    const int lane = threadIdx.x & 31;
+    u32 base = 0;
+    if (lane == leader)
+        base = atomicAdd(counter, (u32)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + (u32)__popc(mask & ((1u << lane) - 1));
 }
 
 __device__ __forceinline__ i32 enter_arc(i32 node, i32 m)
@@ -86,6 +105,8 @@ __device__ __forceinline__ i32 after_arc(i32 c, i32 m, const i32 *par, const i32
 }
 
 // ---- 1. parents and validation --------------------------------------------
+// Children of edge p: the smaller node id in kids[2p], the larger in
+// kids[2p + 1] (any fixed order serves the tour).
 __global__ void flat_parents_kernel(const i32 *ep, const i32 *vp, const float *w, i32 m, i32 n,
                                     i32 *par, i32 *cnt, i32 *kids, FlatCtrl *c)
 {
@@ -113,9 +134,20 @@ __global__ void flat_parents_kernel(const i32 *ep, const i32 *vp, const float *w
             continue;
         }
         par[i] = p;
-        const i32 slot = atomicAdd(&cnt[p], 1);
-        if (slot < 2)
-            kids[2 * (i64)p + slot] = (i32)i;
+        // no return values: the three updates issue as reductions
+        atomicAdd(&cnt[p], 1);
+        atomicMin(&kids[2 * (i64)p], (i32)i);
+        atomicMax(&kids[2 * (i64)p + 1], (i32)i);
+    }
+}
+
+// kids[2e] = INT32_MAX and kids[2e + 1] = -1 (for the min / max above), cnt = 0.
+__global__ void kids_init_kernel(i32 m, i32 *kids, i32 *cnt)
+{
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        reinterpret_cast<int2 *>(kids)[e] = make_int2(INT32_MAX, -1);
+        cnt[e] = 0;
     }
 }
 
@@ -205,9 +237,10 @@ __global__ void rs_pick_kernel(i64 L, i32 *sid_of, i32 *spl, i64 cap, FlatCtrl *
     const i64 head = 2 * (i64)c->root;
     for (i64 a = blockIdx.x * (i64)blockDim.x + threadIdx.x; a < L;
          a += (i64)gridDim.x * blockDim.x) {
-        if (!rs_splitter(a, head))
+        const bool pick = rs_splitter(a, head);
+        const u32 id = warp_append(&c->rs_count, pick);
+        if (!pick)
             continue;
-        const u32 id = atomicAdd(&c->rs_count, 1u);
         if ((i64)id < cap) {
             spl[id] = (i32)a;
             sid_of[a] = (i32)id;
@@ -218,8 +251,10 @@ __global__ void rs_pick_kernel(i64 L, i32 *sid_of, i32 *spl, i64 cap, FlatCtrl *
 }
 
 // seg[i]: next segment (high 32 bits, -1 at the end) | sum of the segment.
-__global__ void rs_walk_kernel(const u64 *arc, u64 *owner_loc, const i32 *sid_of, const i32 *spl,
-                               i64 cap, i64 L, u64 *seg, FlatCtrl *c)
+// Records (segment, sum before it) for every arc in owner_loc.  (Writing it
+// over the arc word just read, in place, measured six times slower.)
+__global__ void rs_walk_kernel(const u64 *arc, u64 *owner_loc, const i32 *sid_of,
+                               const i32 *spl, i64 cap, i64 L, u64 *seg, FlatCtrl *c)
 {
     if (failed(c))
         return;
@@ -251,8 +286,9 @@ __global__ void rs_walk_kernel(const u64 *arc, u64 *owner_loc, const i32 *sid_of
     }
 }
 
+// (segment, sum before) -> suffix sum, into the arc array.
 __global__ void rs_final_kernel(const u64 *owner_loc, const u64 *seg_suf, i64 cap, i64 L,
-                                u64 *suf, FlatCtrl *c)
+                                u64 *arc, FlatCtrl *c)
 {
     if (failed(c))
         return;
@@ -264,7 +300,7 @@ __global__ void rs_final_kernel(const u64 *owner_loc, const u64 *seg_suf, i64 ca
             set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
             continue;
         }
-        suf[a] = (u32)seg_suf[own] - (u32)ol;
+        arc[a] = (u32)seg_suf[own] - (u32)ol;
     }
 }
 
@@ -281,45 +317,182 @@ __global__ void sizes_kernel(const u64 *suf, i32 m, i32 n, i32 *size, FlatCtrl *
         size[e] = e == root ? n : (i32)((u32)suf[2 * e] - (u32)suf[2 * e + 1]);
 }
 
-// ---- 3. starts and anchors ---------------------------------------------------
-__global__ void anchor_init_kernel(i32 m, i32 n, i32 mcs, const i32 *par, const i32 *kids,
-                                   const i32 *size, i32 *jmp, i32 *start, const FlatCtrl *c)
+// ---- 3. cluster starts, the start above every big edge ---------------------------
+__device__ __forceinline__ i32 node_size(i32 node, i32 m, const i32 *size)
+{
+    return node < m ? size[node] : 1;
+}
+
+// start(e): the root, or a big edge whose sibling is big too (both children of
+// a split start clusters).  head(e) = e for a start, -1 until resolved.
+__global__ void start_kernel(i32 m, i32 mcs, const i32 *par, const i32 *kids, const i32 *size,
+                             i32 *start, i32 *head, const FlatCtrl *c)
 {
     if (failed(c))
         return;
     const i32 root = c->root;
-    const i64 N = (i64)m + n;
-    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
-         i += (i64)gridDim.x * blockDim.x) {
-        const i32 p = par[i];
-        const bool big = (i < m ? size[i] : 1) >= mcs;
-        bool st = false;
-        if (i == root) {
-            st = true;
-        } else if (big) {
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        bool st = e == root;
+        if (!st && size[e] >= mcs) {
+            const i32 p = par[e];
             const i32 k0 = kids[2 * (i64)p];
-            const i32 sib = k0 == (i32)i ? kids[2 * (i64)p + 1] : k0;
-            st = (sib < m ? size[sib] : 1) >= mcs;
+            const i32 sib = k0 == (i32)e ? kids[2 * (i64)p + 1] : k0;
+            st = node_size(sib, m, size) >= mcs;
         }
-        const bool anchor = st || (!big && p >= 0 && size[p] >= mcs);
-        jmp[i] = anchor ? (i32)i : p;
-        if (i < m)
-            start[i] = st;
+        start[e] = st;
+        head[e] = st ? (i32)e : -1;
     }
 }
 
-// In place: a node only ever moves up its own chain and anchors point to
-// themselves, so any interleaving reaches the synchronous result or further.
-__global__ void jump_kernel(i32 *jmp, i64 N, const FlatCtrl *c)
+// The big edges of one cluster form a path going up to its start (a big edge
+// with one big child continues its parent's cluster), so the start above
+// every big edge is the head of its path: list ranking again, by a ruling
+// set.  Splitters: the bottom of every path (a big non-start edge with zero
+// or two big children) and about one other big edge in 64; one thread per
+// splitter walks up to the next splitter or to the start; the short lists
+// of segments are resolved by pointer jumping.
+__device__ __forceinline__ bool path_hash_pick(i64 e)
+{
+    u32 h = (u32)e * 0x9E3779B1u;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    return (h & 63u) == 0;
+}
+
+__global__ void path_pick_kernel(i32 m, i32 mcs, const i32 *kids, const i32 *size,
+                                 const i32 *start, i32 *bsid, i32 *spl, i64 cap, FlatCtrl *c)
 {
     if (failed(c))
         return;
-    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        i32 id = -1;
+        bool pick = false;
+        if (size[e] >= mcs && !start[e]) {
+            const int nbig = (node_size(kids[2 * e], m, size) >= mcs) +
+                             (node_size(kids[2 * e + 1], m, size) >= mcs);
+            pick = nbig != 1 || path_hash_pick(e);
+        }
+        const u32 t = warp_append(&c->bp_count, pick);
+        if (pick) {
+            if ((i64)t < cap) {
+                id = (i32)t;
+                spl[t] = (i32)e;
+            } else {
+                set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+            }
+        }
+        bsid[e] = id;
+    }
+}
+
+__global__ void path_walk_kernel(i32 m, const i32 *par, const i32 *start, const i32 *bsid,
+                                 const i32 *spl, i64 cap, i32 *seg_of, i32 *seg_next,
+                                 i32 *seg_head, FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i64 cnt = (i64)c->bp_count < cap ? (i64)c->bp_count : cap;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < cnt;
          i += (i64)gridDim.x * blockDim.x) {
-        const i32 j = jmp[i];
-        const i32 jj = jmp[j];
-        if (jj != j)
-            jmp[i] = jj;
+        i32 cur = spl[i];
+        for (i64 steps = 0;; ++steps) {
+            seg_of[cur] = (i32)i;
+            const i32 nx = par[cur];
+            if (nx < 0 || steps > m) {             // a big non-start edge has a parent
+                set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+                break;
+            }
+            if (start[nx]) {
+                seg_next[i] = -1;
+                seg_head[i] = nx;
+                break;
+            }
+            const i32 sb = bsid[nx];
+            if (sb >= 0) {
+                seg_next[i] = sb;
+                seg_head[i] = -1;
+                break;
+            }
+            cur = nx;
+        }
+    }
+}
+
+// (next, head): head is valid once next = -1.
+__global__ void seg_jump_kernel(i64 cnt, const i32 *nxA, const i32 *hdA, i32 *nxB, i32 *hdB,
+                                u32 *unresolved, const FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    u32 open = 0;
+    for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < cnt;
+         i += (i64)gridDim.x * blockDim.x) {
+        const i32 j = nxA[i];
+        if (j >= 0) {
+            const i32 jj = nxA[j];
+            nxB[i] = jj;
+            hdB[i] = hdA[j];
+            open += jj >= 0;
+        } else {
+            nxB[i] = -1;
+            hdB[i] = hdA[i];
+        }
+    }
+    open = __reduce_add_sync(__activemask(), open);
+    if ((threadIdx.x & 31) == 0 && open)
+        atomicAdd(unresolved, open);
+}
+
+__global__ void path_final_kernel(i32 m, i32 mcs, const i32 *size, const i32 *start,
+                                  const i32 *seg_of, const i32 *hd, i64 cap, i32 *head,
+                                  FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
+         e += (i64)gridDim.x * blockDim.x) {
+        if (size[e] < mcs || start[e])
+            continue;
+        const i32 sg = seg_of[e];
+        const i32 h = (sg >= 0 && sg < cap) ? hd[sg] : -1;
+        if (h < 0)
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+        else
+            head[e] = h;
+    }
+}
+
+// Every leaf leaves its cluster inside the small subtree whose top t has a
+// big parent p: at lambda(p), from the cluster of p.  Those subtrees hold
+// consecutive leaves of the tour, so the record (cluster of p, p) is written
+// at the index of t's first leaf (leaves before it = n - suffix(first arc))
+// and filled forward over the leaf indices.
+constexpr u64 NO_RECORD = ~0ull;
+
+__global__ void anchor_mark_kernel(i32 m, i32 n, i32 mcs, const i32 *par, const i32 *size,
+                                   const i32 *head, const i32 *cid, const u64 *suf, u64 *rec,
+                                   FlatCtrl *c)
+{
+    if (failed(c))
+        return;
+    const i64 N = (i64)m + n;
+    for (i64 t = blockIdx.x * (i64)blockDim.x + threadIdx.x; t < N;
+         t += (i64)gridDim.x * blockDim.x) {
+        if (t < m && size[t] >= mcs)
+            continue;                              // big
+        const i32 p = par[t];
+        if (p < 0 || size[p] < mcs)
+            continue;                              // not the top of a small subtree
+        const i32 h = head[p];
+        const u32 key = (u32)n - (u32)suf[t < m ? 2 * t : 2 * (i64)m + (t - m)];
+        if (h < 0 || key >= (u32)n) {
+            set_status(&c->status, PANDORA_ERR_ITERATION_LIMIT);
+            continue;
+        }
+        rec[key] = ((u64)(u32)cid[h] << 32) | (u32)p;
     }
 }
 
@@ -413,6 +586,100 @@ __global__ void scan_down_kernel(const i32 *in, i64 len, const i32 *bsum, i32 *o
     }
 }
 
+// ---- fill-forward scan of u64 records (3 kernels) ---------------------------------
+// out[i] = the last record at or before i that is not NO_RECORD.
+__device__ __forceinline__ u64 fill_op(u64 earlier, u64 later)
+{
+    return later != NO_RECORD ? later : earlier;
+}
+
+__device__ __forceinline__ u64 block_exclusive_fill(u64 v, u64 *sm, u64 *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o)
+            x = fill_op(y, x);
+    }
+    u64 before = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0)
+        before = NO_RECORD;
+    if (lane == 31)
+        sm[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        u64 t = lane < nw ? sm[lane] : NO_RECORD;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o)
+                t = fill_op(y, t);
+        }
+        sm[lane] = t;
+    }
+    __syncthreads();
+    const u64 warp_before = warp ? sm[warp - 1] : NO_RECORD;
+    *total = sm[nw - 1];
+    __syncthreads();
+    return fill_op(warp_before, before);
+}
+
+__global__ void fill_reduce_kernel(const u64 *in, i64 len, u64 *bagg)
+{
+    __shared__ u64 sm[32];
+    const i64 base = blockIdx.x * (i64)SC_TILE + threadIdx.x * (i64)SC_ITEMS;
+    u64 a = NO_RECORD;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k)
+        if (base + k < len)
+            a = fill_op(a, in[base + k]);
+    u64 total;
+    block_exclusive_fill(a, sm, &total);
+    if (threadIdx.x == 0)
+        bagg[blockIdx.x] = total;
+}
+
+// One block: bagg[b] becomes the record carried into tile b.
+__global__ void fill_top_kernel(u64 *bagg, i64 nb)
+{
+    __shared__ u64 sm[32];
+    const i64 per = (nb + blockDim.x - 1) / blockDim.x;
+    const i64 lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+    u64 a = NO_RECORD;
+    for (i64 i = lo; i < hi; ++i)
+        a = fill_op(a, bagg[i]);
+    u64 total;
+    u64 run = block_exclusive_fill(a, sm, &total);
+    for (i64 i = lo; i < hi; ++i) {
+        const u64 v = bagg[i];
+        bagg[i] = run;
+        run = fill_op(run, v);
+    }
+}
+
+__global__ void fill_down_kernel(u64 *data, i64 len, const u64 *bagg)
+{
+    __shared__ u64 sm[32];
+    const i64 base = blockIdx.x * (i64)SC_TILE + threadIdx.x * (i64)SC_ITEMS;
+    u64 v[SC_ITEMS];
+    u64 a = NO_RECORD;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        v[k] = base + k < len ? data[base + k] : NO_RECORD;
+        a = fill_op(a, v[k]);
+    }
+    u64 total;
+    u64 run = fill_op(bagg[blockIdx.x], block_exclusive_fill(a, sm, &total));
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        run = fill_op(run, v[k]);
+        if (base + k < len)
+            data[base + k] = run;
+    }
+}
+
 // ---- 4. exact stability sums ---------------------------------------------------
 // (host-callable too, so that the arithmetic can be checked without a GPU)
 __host__ __device__ __forceinline__ u64 double_bits(double t)
@@ -497,7 +764,8 @@ __global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32
         if (!start[e])
             continue;
         const i32 k = cid[e];
-        const i32 pk = e == root ? -1 : cid[jmp[par[e]]];
+        const i32 hp = e == root ? -1 : jmp[par[e]];
+        const i32 pk = e == root ? -1 : (hp >= 0 ? cid[hp] : (i32)Kmax);
         if (k >= Kmax || pk >= Kmax) {           // more clusters than n / mcs allows
             set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
             continue;
@@ -551,9 +819,8 @@ __global__ void child_terms_kernel(i32 K, const i32 *cpar, const i32 *csize,
 // accumulator.  Lanes of a warp with the same (cluster, digit position) add
 // their digits first (16-bit halves, so the 32-lane sums cannot overflow),
 // then one lane per group issues the atomics.
-__global__ void leaf_terms_kernel(i32 m, i32 n, const i32 *par, const i32 *jmp, const i32 *cid,
-                                  const float *w, const double *birth, u64 *acc, i32 *lcl,
-                                  FlatCtrl *c)
+__global__ void leaf_terms_kernel(i32 m, i32 n, const u64 *suf, const u64 *rec, const float *w,
+                                  const double *birth, u64 *acc, i32 *lcl, FlatCtrl *c)
 {
     if (failed(c))
         return;
@@ -568,13 +835,20 @@ __global__ void leaf_terms_kernel(i32 m, i32 n, const i32 *par, const i32 *jmp, 
         i32 k = 0;
         bool bad = false;
         if (x < n) {
-            const i32 a = jmp[m + x];
-            const i32 p = par[a];
-            k = cid[jmp[p]];
+            const u32 idx = (u32)n - (u32)suf[2 * (i64)m + x];
+            const u64 r = idx < (u32)n ? rec[idx] : NO_RECORD;
+            k = (i32)(r >> 32);
+            const i32 p = (i32)(u32)r;
+            if (r == NO_RECORD) {
+                bad = true;
+                k = 0;
+            }
             lcl[x] = k;
-            const double t = 1.0 / (double)w[p] - birth[k];
-            if (split_digits(t, j0, dg[0], dg[1], dg[2], bad))
-                key = ((u64)(u32)k << 4) | (u64)j0;
+            if (!bad) {
+                const double t = 1.0 / (double)w[p] - birth[k];
+                if (split_digits(t, j0, dg[0], dg[1], dg[2], bad))
+                    key = ((u64)(u32)k << 4) | (u64)j0;
+            }
         }
         if (bad)
             set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
@@ -1028,10 +1302,13 @@ struct Carve {
 struct FlatLayout {
     FlatCtrl *ctrl;
     i32 *par, *cnt, *kids, *size, *jmp, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
-    u64 *arcA, *arcB;       // tour words, then suffix sums (A); segment owner and offset (B)
+    u64 *arcA, *arcB;       // tour words, then suffix sums (A); (segment, offset) (B)
     i32 *sid_of, *spl;      // ruling set: splitter id per arc, splitter arcs
     u64 *segA, *segB;       // ruling set: segment words
     i64 rs_cap;
+    i32 *bsid, *bspl, *seg_of, *nxA, *nxB, *hdA, *hdB;   // path heads (ruling set)
+    i64 bp_cap;
+    u64 *rec, *bagg;        // leaf records and their fill scan
     i32 *first, *cpar, *ckids, *ccnt, *csize, *cedge, *sel, *upA, *upB, *valA, *valB;
     double *birth, *stab;
     u64 *acc;
@@ -1050,7 +1327,7 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.cnt = cv.take<i32>(m);
     l.kids = cv.take<i32>(2 * m);
     l.size = cv.take<i32>(m);
-    l.jmp = cv.take<i32>(N);
+    l.jmp = cv.take<i32>(m);
     l.start = cv.take<i32>(m);
     l.cid = cv.take<i32>(m);
     l.bsum = cv.take<i32>(nb);
@@ -1065,6 +1342,16 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.spl = cv.take<i32>(l.rs_cap);
     l.segA = cv.take<u64>(l.rs_cap);
     l.segB = cv.take<u64>(l.rs_cap);
+    l.bp_cap = m / 48 + 4096 + 2 * Kmax;
+    l.bsid = cv.take<i32>(m);
+    l.seg_of = cv.take<i32>(m);
+    l.bspl = cv.take<i32>(l.bp_cap);
+    l.nxA = cv.take<i32>(l.bp_cap);
+    l.nxB = cv.take<i32>(l.bp_cap);
+    l.hdA = cv.take<i32>(l.bp_cap);
+    l.hdB = cv.take<i32>(l.bp_cap);
+    l.rec = cv.take<u64>(n);
+    l.bagg = cv.take<u64>(nb);
     l.first = cv.take<i32>(Kmax);
     l.cpar = cv.take<i32>(Kmax);
     l.ckids = cv.take<i32>(2 * Kmax);
@@ -1125,6 +1412,16 @@ void scan_flags(const i32 *in, i64 len, i32 *bsum, i32 *out, i32 *total, cudaStr
 
 // Launches every step on s; returns after reading the status.  The only
 // host synchronisation inside is the read of the cluster count.
+void fill_records(u64 *data, i64 len, u64 *bagg, cudaStream_t s)
+{
+    const i64 nb = (len + SC_TILE - 1) / SC_TILE;
+    if (nb == 0)
+        return;
+    fill_reduce_kernel<<<(unsigned)nb, FT, 0, s>>>(data, len, bagg);
+    fill_top_kernel<<<1, 1024, 0, s>>>(bagg, nb);
+    fill_down_kernel<<<(unsigned)nb, FT, 0, s>>>(data, len, bagg);
+}
+
 int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *w, i64 n,
                 i32 mcs, i64 Kmax, i32 *labels, double *stab_out, i64 *n_clusters,
                 cudaStream_t s)
@@ -1133,7 +1430,7 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
     FlatCtrl *c = l.ctrl;
     const i32 mi = (i32)m, ni = (i32)n;
     cudaMemsetAsync(c, 0, sizeof(FlatCtrl), s);
-    cudaMemsetAsync(l.cnt, 0, sizeof(i32) * m, s);
+    kids_init_kernel<<<grid_for(m), FT, 0, s>>>(mi, l.kids, l.cnt);
 
     // 1. parents and validation
     flat_parents_kernel<<<grid_for(N), FT, 0, s>>>(ep, vp, w, mi, ni, l.par, l.cnt, l.kids, c);
@@ -1155,12 +1452,53 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
         rs_final_kernel<<<grid_for(L), FT, 0, s>>>(l.arcB, in, l.rs_cap, L, l.arcA, c);
         const u64 *suf = l.arcA;
         sizes_kernel<<<grid_for(m), FT, 0, s>>>(suf, mi, ni, l.size, c);
-        // 3. starts, anchors, cluster ids
-        anchor_init_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.kids, l.size, l.jmp,
-                                                      l.start, c);
-        for (int r = ceil_log2(N); r > 0; --r)
-            jump_kernel<<<grid_for(N), FT, 0, s>>>(l.jmp, N, c);
+        // 3. starts, the start above every big edge, cluster ids, leaf records
+        start_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.par, l.kids, l.size, l.start, l.jmp,
+                                                c);
+        cudaMemsetAsync(l.seg_of, 0xFF, sizeof(i32) * m, s);
+        cudaMemsetAsync(l.nxA, 0xFF, sizeof(i32) * l.bp_cap, s);
+        cudaMemsetAsync(l.hdA, 0xFF, sizeof(i32) * l.bp_cap, s);
+        path_pick_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.kids, l.size, l.start, l.bsid,
+                                                    l.bspl, l.bp_cap, c);
+        path_walk_kernel<<<grid_for(l.bp_cap), FT, 0, s>>>(mi, l.par, l.start, l.bsid, l.bspl,
+                                                           l.bp_cap, l.seg_of, l.nxA, l.hdA, c);
+        {
+            // pointer jumping over the segments until every one has its start
+            // (a path of q segments needs ceil(log2 q) rounds; paths are short)
+            FlatCtrl h{};
+            if (cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PANDORA_ERR_CUDA;
+            if (h.status)
+                return h.status;
+            const i64 cnt = (i64)h.bp_count < l.bp_cap ? (i64)h.bp_count : l.bp_cap;
+            i32 *na = l.nxA, *ha = l.hdA, *nb = l.nxB, *hb = l.hdB;
+            for (int r = ceil_log2(cnt) + 1; r > 0 && cnt > 0; --r) {
+                cudaMemsetAsync(&c->unresolved, 0, sizeof(u32), s);
+                seg_jump_kernel<<<grid_for(cnt), FT, 0, s>>>(cnt, na, ha, nb, hb, &c->unresolved,
+                                                             c);
+                i32 *t = na;
+                na = nb;
+                nb = t;
+                t = ha;
+                ha = hb;
+                hb = t;
+                u32 open = 0;
+                if (cudaMemcpyAsync(&open, &c->unresolved, sizeof(u32), cudaMemcpyDeviceToHost,
+                                    s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return PANDORA_ERR_CUDA;
+                if (open == 0)
+                    break;
+            }
+            path_final_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.size, l.start, l.seg_of, ha,
+                                                         l.bp_cap, l.jmp, c);
+        }
         scan_flags(l.start, m, l.bsum, l.cid, &c->n_starts, s);
+        cudaMemsetAsync(l.rec, 0xFF, sizeof(u64) * n, s);
+        anchor_mark_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.size, l.jmp, l.cid,
+                                                      suf, l.rec, c);
+        fill_records(l.rec, n, l.bagg, s);
         cudaMemsetAsync(l.ccnt, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.sel, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.acc, 0, sizeof(u64) * Kmax * NL, s);
@@ -1179,8 +1517,8 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
             return PANDORA_ERR_NOT_A_DENDROGRAM;
         // 4. stabilities
         child_terms_kernel<<<grid_for(K), FT, 0, s>>>(K, l.cpar, l.csize, l.birth, l.acc, c);
-        leaf_terms_kernel<<<grid_for(n), FT, 0, s>>>(mi, ni, l.par, l.jmp, l.cid, w, l.birth,
-                                                     l.acc, l.lcl, c);
+        leaf_terms_kernel<<<grid_for(n), FT, 0, s>>>(mi, ni, suf, l.rec, w, l.birth, l.acc,
+                                                     l.lcl, c);
         finalize_kernel<<<grid_for(K), FT, 0, s>>>(K, l.acc, l.stab, c);
         // 5. excess of mass (K == 1: no candidate, nothing kept)
         if (K >= 3) {
