@@ -66,7 +66,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check", action="store_true",
-                    help="compare the outputs with the oracle after the timed region")
+                    help="check the structure of the outputs after the timed region (one root, "
+                         "edge order, two children per edge, Eq. 1)")
     ap.add_argument("--async-api", action="store_true",
                     help="time pandora_dendrogram_async (worst-case level count, no host sync)")
     ap.add_argument("--flat", type=int, default=0, metavar="MCS",
@@ -84,6 +85,45 @@ def make_tree(spec, n=None):
     if spec["family"] == "hdbscan":
         return inputs.hdbscan_tree(n, spec["seed"])
     return inputs.path_skewed(n, spec["seed"])
+
+
+def dendrogram_structure(u, v, w, ep, vp):
+    """Checks of a dendrogram that need no reference result (numpy, host): one
+    root; every edge later than its children in the total order of Section 3.1
+    (weight, -0.0 before +0.0, index); two children per edge; every vertex's
+    parent is its lightest incident edge (Eq. 1).  Necessary conditions only:
+    element-by-element parity with the oracle is the test suite's job."""
+    import numpy as np
+    m = len(w)
+    n = m + 1
+    out = {"edges": int(m)}
+    if m == 0:
+        out["ok"] = bool(len(vp) == 1 and vp[0] == -1)
+        return out
+    w = np.asarray(w, np.float32)
+    order = np.lexsort((np.arange(m), ~np.signbit(w), w))   # ascending total order
+    rank = np.empty(m, np.int64)
+    rank[order] = np.arange(m)
+    ep = np.asarray(ep, np.int64)
+    vp = np.asarray(vp, np.int64)
+    roots = int((ep == -1).sum())
+    inner = ep >= 0
+    in_range = bool(((ep >= -1) & (ep < m)).all() and ((vp >= 0) & (vp < m)).all())
+    out["one_root"] = roots == 1
+    out["parents_in_range"] = in_range
+    if not in_range:
+        out["ok"] = False
+        return out
+    out["parent_later_in_order"] = bool((rank[ep[inner]] > rank[inner.nonzero()[0]]).all())
+    kids = np.bincount(ep[inner], minlength=m) + np.bincount(vp, minlength=m)
+    out["two_children_each"] = bool((kids == 2).all())
+    lightest = np.full(n, np.iinfo(np.int64).max)
+    np.minimum.at(lightest, np.asarray(u, np.int64), rank)
+    np.minimum.at(lightest, np.asarray(v, np.int64), rank)
+    out["vertex_parent_lightest"] = bool((rank[vp] == lightest).all())
+    out["ok"] = bool(out["one_root"] and out["parent_later_in_order"] and
+                     out["two_children_each"] and out["vertex_parent_lightest"])
+    return out
 
 
 def load_peaks():
@@ -436,10 +476,8 @@ def run_batched(args):
     per_tree_async_ms = a.elapsed_time(z)
     parity = None
     if args.check:
-        # sampled parity at full size: 16 trees (the largest included) against
-        # the oracle one by one, from the planned graph's outputs
-        import oracle
-        oracle.build()
+        # structure of 16 trees (the largest included) from the planned
+        # graph's outputs; oracle parity of batches is in the GPU tests
         g.replay()
         torch.cuda.synchronize()
         pd.workspace_status(ws)
@@ -451,10 +489,11 @@ def run_batched(args):
         ok = True
         for t in pick:
             e0, e1 = int(b.edge_offsets[t]), int(b.edge_offsets[t + 1])
-            oep, ovp = oracle.dendrogram(b.u[e0:e1], b.v[e0:e1], b.w[e0:e1])
-            ok = ok and np.array_equal(ep_h[e0:e1], oep) and \
-                np.array_equal(vp_h[e0 + t:e1 + t + 1], ovp)
-        parity = {"oracle": "kruskal", "trees_checked": len(pick), "equal": bool(ok)}
+            st = dendrogram_structure(b.u[e0:e1], b.v[e0:e1], b.w[e0:e1], ep_h[e0:e1],
+                                      vp_h[e0 + t:e1 + t + 1])
+            ok = ok and st["ok"]
+        parity = {"structure": "root, order, two children, Eq. 1", "trees_checked": len(pick),
+                  "ok": bool(ok)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -826,13 +865,9 @@ def main():
                                  "clusters": int(lab_np.max()) + 1,
                                  "noise_fraction": float((lab_np < 0).mean())}
     if args.check and rank == 0:
-        import oracle
-        oracle.build()
         gep, gvp = pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
-        oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
-        line["parity"] = {"oracle": "kruskal",
-                          "edge_parent_equal": bool(np.array_equal(gep.cpu().numpy(), oep)),
-                          "vertex_parent_equal": bool(np.array_equal(gvp.cpu().numpy(), ovp))}
+        line["structure"] = dendrogram_structure(t.u, t.v, t.w, gep.cpu().numpy(),
+                                                 gvp.cpu().numpy())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -24,3 +24,39 @@ def test_reference_arm_json_line():
     assert d["unit"] == "edges/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["config"]["workload"] == "rrt_1e8"
+
+
+def test_structure_check_accepts_dendrograms_and_rejects_corruptions():
+    """bench.py --check validates outputs without the oracle; the checks must
+    hold on correct dendrograms (from the oracle here, on the CPU) and fail
+    on each kind of corruption."""
+    import importlib.util
+
+    import numpy as np
+
+    import oracle
+    from paper_2401_06089_gb300 import inputs
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    check = bench.dendrogram_structure
+    for seed in range(6):
+        t = inputs.rrt(3000, seed) if seed % 2 else inputs.path(3000, seed, kind="random")
+        w = t.w if seed < 4 else np.where(np.arange(t.m) % 2, 0.0, -0.0).astype(np.float32)
+        ep, vp = oracle.dendrogram(t.u, t.v, w)
+        assert check(t.u, t.v, w, ep, vp)["ok"]
+        e = int(np.flatnonzero(ep >= 0)[seed])
+        bad = ep.copy()
+        bad[e] = -1                                  # two roots
+        assert not check(t.u, t.v, w, bad, vp)["ok"]
+        bad = ep.copy()
+        bad[ep[e]] = e                               # a parent earlier than its child
+        assert not check(t.u, t.v, w, bad, vp)["ok"]
+        badv = vp.copy()
+        x = int(np.flatnonzero(vp != vp[0])[0])
+        badv[x] = vp[0]                              # three children / not the lightest
+        assert not check(t.u, t.v, w, ep, badv)["ok"]
+    one = check(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
+                np.zeros(0, np.int32), np.full(1, -1, np.int32))
+    assert one["ok"]
