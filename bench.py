@@ -474,7 +474,7 @@ def run_batched(args):
     z.record(stream)
     torch.cuda.synchronize()
     per_tree_async_ms = a.elapsed_time(z)
-    parity = None
+    structure = None
     if args.check:
         # structure of 16 trees (the largest included) from the planned
         # graph's outputs; oracle parity of batches is in the GPU tests
@@ -492,8 +492,8 @@ def run_batched(args):
             st = dendrogram_structure(b.u[e0:e1], b.v[e0:e1], b.w[e0:e1], ep_h[e0:e1],
                                       vp_h[e0 + t:e1 + t + 1])
             ok = ok and st["ok"]
-        parity = {"structure": "root, order, two children, Eq. 1", "trees_checked": len(pick),
-                  "ok": bool(ok)}
+        structure = {"checks": "root, order, two children, Eq. 1", "trees_checked": len(pick),
+                     "ok": bool(ok)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -517,7 +517,7 @@ def run_batched(args):
         "blocking_dispatch_ms": dispatch_ms,
         "forest_async_graph_ms": forest_graph_ms,
         "tuning": tuning,
-        "parity": parity,
+        "structure": structure,
         "blocking_kernels": kern,
         "levels": bstats["level_edges"],
         "clocks": sampler.summary(),

@@ -12,6 +12,9 @@ GPU library never imports it and shares no code with it.
 * ``cartesian_path``: closed form for path trees (Theorem 1), ``cartesian.c``.
 * ``contraction``: a plain numpy model of the paper's alpha-edge contraction
   levels and multilevel expansion (Sections 3.2-3.3), for per-level checks.
+* ``flat``: HDBSCAN* flat clusters of a dendrogram (the optional last step of
+  the pipeline in Section 6.5, after Campello et al.), plain Python with exact
+  rational sums.
 """
 from __future__ import annotations
 
