@@ -16,12 +16,13 @@
 //     parent later than its child in (weight, index) order, weights > 0);
 //  2. leaf counts: Euler tour of the dendrogram (down/up arc per edge, one
 //     arc per leaf), suffix sums by list ranking over a sparse ruling set;
-//  3. per node: big = leaf count >= mcs; cluster starts (the root, and both
-//     children of an edge whose children are both big); anchors (starts, and
-//     small nodes under a big parent); nearest anchor above every node by
-//     pointer jumping.  A vertex's anchor is the top of the small part it
-//     falls off in; that part's parent edge p gives the leave lambda and the
-//     cluster (p's anchor, a start);
+//  3. big = leaf count >= mcs; cluster starts (the root, and both children
+//     of an edge whose children are both big); the start above every big
+//     edge (the big edges of a cluster form one upward path: a second ruling
+//     set); for every vertex, the top t of the small subtree it falls off in
+//     (t has a big parent p; p gives the leave lambda and, through its start,
+//     the cluster), found by a fill-forward scan over the leaf indices of the
+//     tour, since each such subtree holds consecutive leaves;
 //  4. stabilities: every term (a leaving point's fl(lambda - birth), and
 //     size(D) copies of a child cluster's fl(birth(D) - birth(C))) is a
 //     multiple of 2^-180 below 2^181 (lambda = 1/w of a float32 w lies in
@@ -752,7 +753,7 @@ __host__ __device__ __forceinline__ bool split_digits(double t, int &j0, u32 &d0
 }
 
 __global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32 *cid,
-                                    const i32 *par, const i32 *jmp, const i32 *size,
+                                    const i32 *par, const i32 *head, const i32 *size,
                                     const float *w, i32 *cpar, i32 *ckids, i32 *ccnt, i32 *csize,
                                     i32 *cedge, double *birth, FlatCtrl *c)
 {
@@ -764,7 +765,7 @@ __global__ void cluster_init_kernel(i32 m, i64 Kmax, const i32 *start, const i32
         if (!start[e])
             continue;
         const i32 k = cid[e];
-        const i32 hp = e == root ? -1 : jmp[par[e]];
+        const i32 hp = e == root ? -1 : head[par[e]];
         const i32 pk = e == root ? -1 : (hp >= 0 ? cid[hp] : (i32)Kmax);
         if (k >= Kmax || pk >= Kmax) {           // more clusters than n / mcs allows
             set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
@@ -1301,7 +1302,7 @@ struct Carve {
 
 struct FlatLayout {
     FlatCtrl *ctrl;
-    i32 *par, *cnt, *kids, *size, *jmp, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
+    i32 *par, *cnt, *kids, *size, *head, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
     u64 *arcA, *arcB;       // tour words, then suffix sums (A); (segment, offset) (B)
     i32 *sid_of, *spl;      // ruling set: splitter id per arc, splitter arcs
     u64 *segA, *segB;       // ruling set: segment words
@@ -1327,7 +1328,7 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.cnt = cv.take<i32>(m);
     l.kids = cv.take<i32>(2 * m);
     l.size = cv.take<i32>(m);
-    l.jmp = cv.take<i32>(m);
+    l.head = cv.take<i32>(m);
     l.start = cv.take<i32>(m);
     l.cid = cv.take<i32>(m);
     l.bsum = cv.take<i32>(nb);
@@ -1453,7 +1454,7 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
         const u64 *suf = l.arcA;
         sizes_kernel<<<grid_for(m), FT, 0, s>>>(suf, mi, ni, l.size, c);
         // 3. starts, the start above every big edge, cluster ids, leaf records
-        start_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.par, l.kids, l.size, l.start, l.jmp,
+        start_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.par, l.kids, l.size, l.start, l.head,
                                                 c);
         cudaMemsetAsync(l.seg_of, 0xFF, sizeof(i32) * m, s);
         cudaMemsetAsync(l.nxA, 0xFF, sizeof(i32) * l.bp_cap, s);
@@ -1492,18 +1493,18 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
                     break;
             }
             path_final_kernel<<<grid_for(m), FT, 0, s>>>(mi, mcs, l.size, l.start, l.seg_of, ha,
-                                                         l.bp_cap, l.jmp, c);
+                                                         l.bp_cap, l.head, c);
         }
         scan_flags(l.start, m, l.bsum, l.cid, &c->n_starts, s);
         cudaMemsetAsync(l.rec, 0xFF, sizeof(u64) * n, s);
-        anchor_mark_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.size, l.jmp, l.cid,
+        anchor_mark_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.size, l.head, l.cid,
                                                       suf, l.rec, c);
         fill_records(l.rec, n, l.bagg, s);
         cudaMemsetAsync(l.ccnt, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.sel, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.acc, 0, sizeof(u64) * Kmax * NL, s);
         cudaMemsetAsync(l.first, 0x7F, sizeof(i32) * Kmax, s);
-        cluster_init_kernel<<<grid_for(m), FT, 0, s>>>(mi, Kmax, l.start, l.cid, l.par, l.jmp,
+        cluster_init_kernel<<<grid_for(m), FT, 0, s>>>(mi, Kmax, l.start, l.cid, l.par, l.head,
                                                        l.size, w, l.cpar, l.ckids, l.ccnt,
                                                        l.csize, l.cedge, l.birth, c);
         FlatCtrl h{};
