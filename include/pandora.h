@@ -330,9 +330,10 @@ int pandora_profile_read(pandora_profile *out);
  * min_cluster_size >= 2 (else PANDORA_ERR_INVALID_ARGUMENT); at most
  * PANDORA_FLAT_MAX_VERTICES points (else PANDORA_ERR_SIZE_LIMIT).  The input
  * is validated on the device: PANDORA_ERR_BAD_WEIGHT,
- * PANDORA_ERR_NOT_A_DENDROGRAM.  Scratch (about 105 bytes per point plus
- * 180 bytes per possible cluster, 2 n_vertices / min_cluster_size + 1)
- * comes from the library's stream-ordered pool.  Blocking: returns after the work on `stream` has finished.
+ * PANDORA_ERR_NOT_A_DENDROGRAM.  Scratch (130 bytes per point plus 640 bytes
+ * per possible cluster, 2 n_vertices / min_cluster_size + 1: 21 GB for 10^8
+ * points at min_cluster_size 16, 77 GB at 2) comes from the library's
+ * stream-ordered pool; PANDORA_ERR_OUT_OF_MEMORY when it does not fit.  Blocking: returns after the work on `stream` has finished.
  */
 #define PANDORA_FLAT_MAX_VERTICES 536870912
 int pandora_hdbscan_labels(const int32_t *edge_parent, const int32_t *vertex_parent,
