@@ -1386,16 +1386,20 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     return l;
 }
 
+// Grid of a grid-stride kernel: one block per FT items, at most 8 blocks per
+// SM of the device current at the first call (thread-safe initialisation).
 int grid_for(i64 count)
 {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms <= 0)
-            sms = 148;
-    }
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        return n;
+    }();
     const i64 want = (count + FT - 1) / FT;
     const i64 cap = (i64)sms * 8;
     return (int)(want < 1 ? 1 : want < cap ? want : cap);
