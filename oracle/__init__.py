@@ -15,6 +15,8 @@ GPU library never imports it and shares no code with it.
 * ``flat``: HDBSCAN* flat clusters of a dendrogram (the optional last step of
   the pipeline in Section 6.5, after Campello et al.), plain Python with exact
   rational sums.
+* ``emst``: the mutual-reachability minimum spanning tree of a point set (the
+  step before the dendrogram in Section 6.5), plain numpy, O(n^2).
 """
 from __future__ import annotations
 
