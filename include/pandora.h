@@ -226,7 +226,10 @@ int pandora_workspace_status(const void *workspace, void *stream);
  *
  * The first call on a device looks up the device address of the array on
  * that device (cudaGetSymbolAddress, with the device current); make that
- * first call before any stream capture.  Every call reuses the same array
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: it belongs to the device's primary context, so the entry
+ * point must not be used after cudaDeviceReset or from a non-primary
+ * context.  Every call reuses the same array
  * and leaves its contents behind; each call clears what it needs zeroed, but
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on the array and must be serialised by the caller.  Blocking, like

@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     profile_read,
     profile_start,
     load_library,
+    membench,
     set_tuning,
     status_string,
     workspace_size,

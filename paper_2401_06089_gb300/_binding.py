@@ -105,13 +105,15 @@ def load_library():
         lib.pandora_get_tuning.argtypes = [P]
         lib.pandora_hdbscan_labels.argtypes = [P, P, P, I64, ctypes.c_int32, P, P,
                                                ctypes.POINTER(I64), P]
+        lib.pandora_membench.argtypes = [ctypes.c_int, P, P, P, I64, I64, I64, ctypes.c_uint64,
+                                         ctypes.c_int, P]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
                      "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
                      "pandora_dendrogram_batched_planned", "pandora_dendrogram_host",
-                     "pandora_hdbscan_labels"):
+                     "pandora_hdbscan_labels", "pandora_membench"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     _apply_default_tuning()
@@ -483,3 +485,32 @@ def workspace_status(workspace, raise_on_error: bool = True) -> int:
     if st and raise_on_error:
         raise PandoraError(st, "device status")
     return st
+
+
+MEMBENCH_KINDS = {"gather32": 0, "gather64": 1, "scatter32": 2, "scatter64": 3,
+                  "atomicmin64": 4, "copy32": 5}
+
+
+def membench(kind: str, buf, *, n_access: int, window: int = 0, seed: int = 0,
+             blocks_per_sm: int = 8, dst=None, sink=None) -> None:
+    """Enqueue one random-access micro-benchmark kernel (``pandora_membench``)
+    on the current stream: ``n_access`` accesses of ``kind`` to ``buf`` (a
+    CUDA tensor of 4- or 8-byte elements) at hashed positions; the caller
+    times it with CUDA events."""
+    torch = _torch()
+    if kind not in MEMBENCH_KINDS:
+        raise ValueError(f"unknown kind {kind!r}")
+    if not (isinstance(buf, torch.Tensor) and buf.is_cuda and buf.is_contiguous()):
+        raise ValueError("buf must be a contiguous CUDA tensor")
+    width = 8 if kind.endswith("64") else 4
+    if buf.element_size() != width:
+        raise TypeError(f"{kind} needs {width}-byte elements")
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int32, device=buf.device)
+    lib = load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(buf.device).cuda_stream)
+    st = lib.pandora_membench(MEMBENCH_KINDS[kind], _ptr(buf), _ptr(dst), _ptr(sink),
+                              buf.numel(), int(n_access), int(window), int(seed),
+                              int(blocks_per_sm), stream)
+    if st:
+        raise PandoraError(st, "pandora_membench")

@@ -41,6 +41,8 @@ struct Ctrl {
     u32 mark_count[MARK_MAX_BUCKETS];
     u32 mark_cursor[MARK_MAX_BUCKETS];
     u64 mark_base[MARK_MAX_BUCKETS + 1];
+    // bucketed link: write cursors of the caller-id buckets
+    u32 link_cursor[MARK_MAX_BUCKETS];
 };
 
 // Element count produced on the device, clamped to the buffer capacity the
@@ -204,6 +206,21 @@ __device__ __forceinline__ i64 tree_of_edge(const i64 *__restrict__ off, i64 n_t
     while (lo < hi) {
         i64 mid = (lo + hi + 1) >> 1;
         if (__ldg(off + mid) <= e)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tree id of a level-0 vertex in forest mode: tree t owns the vertices
+// [off[t] + t, off[t+1] + t + 1).
+__device__ __forceinline__ i64 tree_of_vertex(const i64 *__restrict__ off, i64 n_trees, i64 x)
+{
+    i64 lo = 0, hi = n_trees - 1;
+    while (lo < hi) {
+        i64 mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) + mid <= x)
             lo = mid;
         else
             hi = mid - 1;

@@ -130,10 +130,30 @@ struct LevelParams {
     u32 *mark_count;       // Ctrl::mark_count (zeroed per level)
     u32 *mark_cursor;      // Ctrl::mark_cursor (zeroed per level)
     u64 *mark_base;        // Ctrl::mark_base
+    // level 0 with bucketed marking: the records also carry the caller id of
+    // their edge, and after the minima are applied a pass over the records in
+    // bucket order finds the record that won at each vertex and
+    //   - sets the edge's bit for that endpoint in eflag (2 bits per edge by
+    //     rank: bit 0 lightest at the first endpoint, bit 1 at the second;
+    //     Eq. 2 reads them: alpha = no bit, leaf edge = both bits),
+    //   - writes vertex_parent (Eq. 1) from the record's caller id,
+    // so that ptr_init and compact need no random read to classify an edge.
+    // eflag == nullptr: classify by reading the endpoints' words.
+    u32 *rec_c;            // [2 m] incidence records: caller edge id
+    u32 *eflag;            // [ceil(m / 16)] zeroed
+    // forests, level 0: roots found per tree and the dense id of one of them
+    // (zeroed counts).  A tree with a single root is one supervertex, so a
+    // vertex whose bounded walk does not reach a root takes that id instead
+    // of going to union-find (the whole level of such a tree is one chain,
+    // Section 3.2).  A single tree uses the level's root count instead.
+    u32 *tree_roots;       // [n_trees]
+    i32 *tree_root_id;     // [n_trees]
 };
 
+__host__ __device__ inline i64 eflag_words(i64 m) { return (m + 15) / 16; }
+
 void launch_init_level(const LevelParams &p, cudaStream_t s);   // min_word = NO_EDGE
-void launch_mark(const LevelParams &p, cudaStream_t s);
+void launch_mark(const LevelParams &p, cudaStream_t s);   // with eflag: also the flag pass
 void launch_ptr_init(const LevelParams &p, cudaStream_t s);
 void launch_compress(const LevelParams &p, cudaStream_t s);   // walk + union-find fallback
 void launch_compact(const LevelParams &p, cudaStream_t s);
@@ -173,6 +193,15 @@ struct LinkParams {
     i32 *edge_parent;
     const i64 *edge_off;
     i64 n_trees;
+    // bucketed link (n_buckets > 0): the (edge, parent) pairs are first
+    // written grouped by caller-id bucket (2^bucket_shift ids, whose
+    // edge_parent range stays in L2), then applied bucket after bucket.
+    // The caller ids are a permutation of [0, m), so bucket b holds exactly
+    // the ids [b << shift, (b + 1) << shift) and starts at rec + (b << shift).
+    int bucket_shift;
+    int n_buckets;
+    int2 *rec;             // [m] (edge, parent) pairs by bucket
+    u32 *cursor;           // [n_buckets] write cursors, zeroed
 };
 
 void launch_link(const LinkParams &p, cudaStream_t s);

@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(MARK_MAX_BUCKETS) mark_prefix_kernel(const Lev
 }
 
 // Dynamic shared memory of a scatter tile: the tile's records staged in
-// bucket order (vertex, word, bucket) so that every bucket's run is written
-// to global memory contiguously.
+// bucket order (vertex, word, bucket; on level 0 with flags also the caller
+// id) so that every bucket's run is written to global memory contiguously.
 constexpr size_t MB_SMEM = (size_t)2 * MB_TILE * (8 + 4 + 2);
+constexpr size_t MB_SMEM_C = (size_t)2 * MB_TILE * (8 + 4 + 4 + 2);
 
 template <bool LEVEL0>
 __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
@@ -210,9 +211,12 @@ __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
     if (loop_closed(p))
         return;
     extern __shared__ __align__(16) unsigned char mb_smem[];
+    constexpr bool CID = LEVEL0;   // records carry caller ids when p.rec_c is set
+    const bool with_c = CID && p.rec_c != nullptr;
     u64 *st_w = (u64 *)mb_smem;
     u32 *st_x = (u32 *)(st_w + 2 * MB_TILE);
-    unsigned short *st_b = (unsigned short *)(st_x + 2 * MB_TILE);
+    u32 *st_c = st_x + 2 * MB_TILE;   // only used with_c
+    unsigned short *st_b = (unsigned short *)(st_x + (with_c ? 4 : 2) * MB_TILE);
     __shared__ u32 s_cnt[MARK_MAX_BUCKETS];
     __shared__ u32 s_off[MARK_MAX_BUCKETS];
     __shared__ u64 s_gbase[MARK_MAX_BUCKETS];
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
             s_cnt[b] = 0;
         __syncthreads();
         int2 e[MB_TILE_ITEMS];
-        u32 r[MB_TILE_ITEMS], sa[MB_TILE_ITEMS], sb[MB_TILE_ITEMS];
+        u32 r[MB_TILE_ITEMS], sa[MB_TILE_ITEMS], sb[MB_TILE_ITEMS], cid[MB_TILE_ITEMS];
         const i64 t0 = tile * MB_TILE;
         const int count = (int)min((i64)MB_TILE, m - t0);
 #pragma unroll
@@ -234,6 +238,8 @@ __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
             const int k = it * 256 + threadIdx.x;
             if (k < count) {
                 e[it] = p.ab[t0 + k];
+                if (with_c)
+                    cid[it] = p.perm[t0 + k];
                 r[it] = LEVEL0 ? (u32)(t0 + k) : p.er[t0 + k];
                 sa[it] = atomicAdd(&s_cnt[mark_bucket(p, e[it].x)], 1u);
                 sb[it] = atomicAdd(&s_cnt[mark_bucket(p, e[it].y)], 1u);
@@ -275,6 +281,10 @@ __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
                 st_x[jb] = (u32)e[it].y;
                 st_w[jb] = ra | ((u64)(u32)e[it].x << 1) | 1u;   // at e.y: side 1
                 st_b[jb] = (unsigned short)bb;
+                if (with_c) {
+                    st_c[ja] = cid[it];
+                    st_c[jb] = cid[it];
+                }
             }
         }
         __syncthreads();
@@ -284,6 +294,8 @@ __global__ void __launch_bounds__(256) mark_scatter_kernel(const LevelParams p)
             if (g < cap) {
                 p.rec_x[g] = st_x[j];
                 p.rec_w[g] = st_w[j];
+                if (with_c)
+                    p.rec_c[g] = st_c[j];
             }
         }
         __syncthreads();   // staging and counters reused by the next tile
@@ -331,6 +343,64 @@ __global__ void __launch_bounds__(256) mark_apply_kernel(const LevelParams p)
     }
 }
 
+// Level 0 with flags: the records again in bucket order (the words of the
+// bucket in progress stay in L2).  The record equal to its vertex's final
+// word is the vertex's lightest incidence: it sets that endpoint's bit of the
+// edge in eflag (2 bits per edge, a word array of m / 4 bytes that fits in
+// L2) and writes the vertex's parent, the edge's caller id (Eq. 1).
+template <bool FOREST>
+__global__ void __launch_bounds__(256) mark_flags_kernel(const LevelParams p)
+{
+    if (loop_closed(p))
+        return;
+    __shared__ u32 s_tile;
+    const i64 total = min((i64)p.mark_base[p.mark_buckets], 2 * p.m_cap);
+    const i64 chunks = (total + MB_TILE - 1) / MB_TILE;
+    const i64 n = dev_count(p.d_n, p.n_cap);
+    const i64 m = dev_count(p.d_m, p.m_cap);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(p.tile_counter + 3, 1u);
+        __syncthreads();
+        const i64 c = s_tile;
+        if (c >= chunks)
+            break;
+        u32 x[MB_TILE_ITEMS], cid[MB_TILE_ITEMS];
+        u64 w[MB_TILE_ITEMS], cur[MB_TILE_ITEMS];
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it) {
+            const i64 j = c * MB_TILE + it * 256 + threadIdx.x;
+            x[it] = 0xFFFFFFFFu;
+            if (j < total) {
+                x[it] = p.rec_x[j];
+                w[it] = p.rec_w[j];
+                cid[it] = p.rec_c[j];
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it)
+            cur[it] = (i64)x[it] < n ? p.min_word[x[it]] : NO_EDGE;
+#pragma unroll
+        for (int it = 0; it < MB_TILE_ITEMS; ++it) {
+            if ((i64)x[it] >= n || cur[it] != w[it])
+                continue;
+            const u64 r = w[it] >> 32;
+            if ((i64)r < m)
+                atomicOr(p.eflag + (r >> 4), 1u << (2 * (u32)(r & 15) + (u32)(w[it] & 1u)));
+            i32 par = (i32)cid[it];
+            if (FOREST)
+                par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, par));
+            p.vertex_parent[x[it]] = par;
+        }
+    }
+}
+
+__device__ __forceinline__ u32 eflag_of(const u32 *eflag, u64 r)
+{
+    return (__ldg(eflag + (r >> 4)) >> (2 * (u32)(r & 15))) & 3u;
+}
+
 // Claims the next tile of a dynamically scheduled kernel (tile ids are handed
 // out in launch order, which keeps the look-back deadlock-free).
 __device__ __forceinline__ u32 claim_tile(u32 *counter, u32 *s_tile)
@@ -375,11 +445,15 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
                 } else {
                     // a leaf edge (lightest at both ends) closes a 2-cycle; its
                     // smaller endpoint becomes the root of the component
-                    const u64 wy = p.min_word[y];
-                    root[it] = ((u32)(wy >> 32) == r) && ((i32)x < y);
+                    bool leaf;
+                    if (LEVEL0 && p.eflag)
+                        leaf = eflag_of(p.eflag, r) == 3u;
+                    else
+                        leaf = (u32)(p.min_word[y] >> 32) == r;
+                    root[it] = leaf && ((i32)x < y);
                     nxt[it] = y;
                 }
-                if (LEVEL0) {
+                if (LEVEL0 && !p.eflag) {   // with flags the flag pass wrote it
                     i32 par = (i32)__ldg(p.perm + r);   // Eq. 1, caller edge id
                     if (FOREST)
                         par -= (i32)__ldg(p.edge_off + tree_of_edge(p.edge_off, p.n_trees, par));
@@ -398,6 +472,15 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
             const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
             if (x < n)
                 p.ptr[x] = root[it] ? ~(i32)rank[it] : nxt[it];
+            if (LEVEL0 && FOREST && p.tree_roots) {
+                // roots per tree, one atomic per tree and warp
+                const i64 t = root[it] ? tree_of_vertex(p.edge_off, p.n_trees, x) : -1;
+                const u32 peers = __match_any_sync(0xFFFFFFFFu, (unsigned long long)t);
+                if (root[it] && (threadIdx.x & 31) == __ffs(peers) - 1) {
+                    atomicAdd(p.tree_roots + t, (u32)__popc(peers));
+                    p.tree_root_id[t] = (i32)rank[it];
+                }
+            }
         }
         if (threadIdx.x == 0 && (i64)tile == tiles - 1)
             *p.d_n_next = base + total;
@@ -465,6 +548,23 @@ __global__ void __launch_bounds__(256) compress_walk_kernel(const LevelParams p)
                     break;
                 }
                 cur = pc;
+            }
+            if (!done) {
+                // a component with the level's (or the tree's) only root: no
+                // union-find needed
+                if (p.n_trees == 1) {
+                    if (*(const volatile u64 *)p.d_n_next == 1) {
+                        res = ~0;
+                        done = true;
+                    }
+                } else if (LEVEL0 && p.tree_roots) {
+                    const i64 t = tree_of_vertex(p.edge_off, p.n_trees, x);
+                    if (p.tree_roots[t] == 1u) {
+                        res = ~p.tree_root_id[t];
+                        done = true;
+                    }
+                }
+                cur = -1;
             }
             if (done) {
                 write_supervertex<LEVEL0>(p, x, ~res);
@@ -625,6 +725,22 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
             // the edge is not the lightest at the first.
             u32 rank_a, rank_b;
             i32 va, vb;
+            if (LEVEL0 && p.eflag) {
+                // the flags say which endpoint's word holds the supervertex
+                const u32 f = eflag_of(p.eflag, r);
+                if (f) {
+                    p.lev[r] = (unsigned char)p.level;
+                    p.start[r] = (i32)(u32)p.min_word[(f & 1u) ? e.x : e.y];
+                    continue;
+                }
+                va = (i32)(u32)p.min_word[e.x];
+                vb = (i32)(u32)p.min_word[e.y];
+                if (va == vb)
+                    set_status(p.status, PANDORA_ERR_NOT_A_TREE);   // a cycle closed up
+                alpha[it] = true;
+                nab[it] = make_int2(va, vb);
+                continue;
+            }
             if (LEVEL0) {
                 const u64 wa = p.min_word[e.x];
                 rank_a = (u32)(wa >> 32);
@@ -729,19 +845,26 @@ void launch_mark(const LevelParams &p, cudaStream_t s)
         const unsigned long long bit = 1ull << (dev & 63);
         if (!(attr_done.load() & bit)) {
             cudaFuncSetAttribute(mark_scatter_kernel<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM_C);
             cudaFuncSetAttribute(mark_scatter_kernel<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MB_SMEM);
             attr_done.fetch_or(bit);
         }
         if (p.level == 0)
-            mark_scatter_kernel<true><<<sb, 256, MB_SMEM, s>>>(p);
+            mark_scatter_kernel<true><<<sb, 256, p.rec_c ? MB_SMEM_C : MB_SMEM, s>>>(p);
         else
             mark_scatter_kernel<false><<<sb, 256, MB_SMEM, s>>>(p);
         i64 ab = (2 * p.m_grid + MB_TILE - 1) / MB_TILE;
         if (ab > 152 * PANDORA_MARK_APPLY_BPS)
             ab = 152 * PANDORA_MARK_APPLY_BPS;
-        mark_apply_kernel<<<(unsigned)(ab < 1 ? 1 : ab), 256, 0, s>>>(p);
+        const unsigned apply_blocks = (unsigned)(ab < 1 ? 1 : ab);
+        mark_apply_kernel<<<apply_blocks, 256, 0, s>>>(p);
+        if (p.level == 0 && p.eflag && p.rec_c) {
+            if (p.edge_off)
+                mark_flags_kernel<true><<<apply_blocks, 256, 0, s>>>(p);
+            else
+                mark_flags_kernel<false><<<apply_blocks, 256, 0, s>>>(p);
+        }
         return;
     }
     i64 b = (p.m_grid + 255) / 256;

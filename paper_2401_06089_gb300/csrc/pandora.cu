@@ -147,12 +147,22 @@ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 #define PANDORA_MARK_BUCKET_SHIFT 22
 #endif
 constexpr i64 MARK_DIRECT_MAX_VERTICES = PANDORA_MARK_DIRECT_MAX;
+// Link stores edge_parent by caller-id buckets of 2^LINK_BUCKET_SHIFT ids
+// (16 MB of edge_parent each) above LINK_BUCKET_MIN_EDGES edges.
+#ifndef PANDORA_LINK_BUCKET_MIN
+#define PANDORA_LINK_BUCKET_MIN (i64(1) << 25)
+#endif
+#ifndef PANDORA_LINK_BUCKET_SHIFT
+#define PANDORA_LINK_BUCKET_SHIFT 22
+#endif
+constexpr i64 LINK_BUCKET_MIN_EDGES = PANDORA_LINK_BUCKET_MIN;
+constexpr int LINK_BUCKET_SHIFT = PANDORA_LINK_BUCKET_SHIFT;
 constexpr int MARK_BUCKET_SHIFT = PANDORA_MARK_BUCKET_SHIFT;
 
 struct Layout {
     size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, ptr;
     size_t deep, uf, root_of;
-    size_t kept_rec, abX, erX, abY, erY, lev, start, total;
+    size_t kept_rec, abX, erX, abY, erY, lev, start, eflag, troots, total;
     i64 kept_cap, half_cap, lb_words;
 };
 
@@ -193,6 +203,8 @@ Layout make_layout(i64 M, i64 T)
     L.erY = take(L.half_cap * 4);
     L.lev = take(M);
     L.start = take(M * 4);
+    L.eflag = take(eflag_words(M) * 4);
+    L.troots = take(T * 8);   // tree_roots, tree_root_id (forests)
     L.total = off + 256;   // slack for aligning an unaligned base
     return L;
 }
@@ -483,6 +495,11 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         if (l == 0) {
             P.perm = perm;
             P.vertex_parent = vp;
+            if (T > 1) {
+                P.tree_roots = (u32 *)(base + L.troots);
+                P.tree_root_id = (i32 *)(base + L.troots) + T;
+                PANDORA_CUDA(cudaMemsetAsync(P.tree_roots, 0, (size_t)T * 4, s));
+            }
         } else {
             if (kept_used + n_cap > L.kept_cap)
                 return PANDORA_ERR_NOT_A_TREE;   // only reachable in blocking mode
@@ -530,12 +547,22 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
                 PANDORA_CUDA(cudaMemsetAsync(ctrl->mark_count, 0,
                                              sizeof(ctrl->mark_count) + sizeof(ctrl->mark_cursor),
                                              s));
+            // level 0: the records also carry caller ids (in the next-level
+            // edge arrays abX .. erY, written only by compact) and a flag pass
+            // classifies every edge for Eq. 2 and writes vertex_parent
+            const size_t next_region = L.erY + (size_t)L.half_cap * 4 - L.abX;
+            if (l == 0 && P.mark_buckets > 0 && (size_t)(2 * m_cap) * 4 <= next_region) {
+                P.rec_c = (u32 *)(base + L.abX);
+                P.eflag = (u32 *)(base + L.eflag);
+                PANDORA_CUDA(cudaMemsetAsync(P.eflag, 0, (size_t)eflag_words(M) * 4, s));
+            }
         }
         PANDORA_CUDA(cudaMemsetAsync(
             lb, 0, (size_t)(level_tiles(n_grid) + 1 + level_tiles(m_grid) + 1) * 8, s));
-        PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 12, s));
+        PANDORA_CUDA(cudaMemsetAsync(ctrl->tile_counter, 0, 16, s));
         timer.launch(K_INIT_LEVEL, n_grid, [&] { launch_init_level(P, s); });
-        timer.launch(K_MARK, m_grid, P.mark_buckets > 0 ? 4 : 1, [&] { launch_mark(P, s); });
+        timer.launch(K_MARK, m_grid, P.mark_buckets > 0 ? (P.eflag ? 5 : 4) : 1,
+                     [&] { launch_mark(P, s); });
         timer.launch(K_PTR_INIT, n_grid, [&] { launch_ptr_init(P, s); });
         if (l == 0)   // vertex_parent is final after level 0's ptr_init
             if (int e = overlap_vp_copy(ov, vp, N, s))
@@ -642,7 +669,19 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     K.edge_parent = ep;
     K.edge_off = d_off;
     K.n_trees = T;
-    timer.launch(K_LINK, M, [&] { launch_link(K, s); });
+    // bucketed link when edge_parent is well above L2; the pairs go to the
+    // level-0 endpoint array (8 bytes per edge), idle after the level loop
+    if (M > LINK_BUCKET_MIN_EDGES) {
+        K.bucket_shift = LINK_BUCKET_SHIFT;
+        K.n_buckets = (int)((M + (i64(1) << LINK_BUCKET_SHIFT) - 1) >> LINK_BUCKET_SHIFT);
+        K.rec = ab0;
+        K.cursor = ctrl->link_cursor;
+        if (K.n_buckets > MARK_MAX_BUCKETS)
+            K.n_buckets = 0;
+        else
+            PANDORA_CUDA(cudaMemsetAsync(ctrl->link_cursor, 0, sizeof(ctrl->link_cursor), s));
+    }
+    timer.launch(K_LINK, M, K.n_buckets > 0 ? 2 : 1, [&] { launch_link(K, s); });
     PANDORA_CUDA(cudaGetLastError());
     if (!blocking)
         return PANDORA_OK;

@@ -60,43 +60,77 @@ __device__ __forceinline__ u32 digit_exclusive_scan(u32 x, u32 *s_warp)
     return prefix + incl - x;
 }
 
+// Digit histograms of the weight keys for all four passes, in one read of the
+// weights.  Each thread keeps 16 bytes of weights in flight per iteration
+// (one float4 when the array is 16-byte aligned) so that enough loads are
+// outstanding to stream at DRAM speed, and each warp counts into its own
+// copy of the histograms.  Lanes with equal top digits are merged first
+// (__match_any_sync): the top digit (sign and high exponent bits) of weights
+// in a narrow range takes only a few values, and equal addresses in one
+// shared-memory atomic serialise.
+constexpr int HIST_WARPS = 8;
+__device__ __forceinline__ void hist_count(u32 (*h)[4 * RADIX], int warp, u32 k, bool valid)
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (valid)
+            atomicAdd(&h[warp][q * RADIX + ((k >> (8 * q)) & 255u)], 1u);
+    const u32 d = valid ? k >> 24 : 256u;   // 256: no count
+    const u32 peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (valid && (threadIdx.x & 31) == (u32)(__ffs(peers) - 1))
+        atomicAdd(&h[warp][3 * RADIX + d], (u32)__popc(peers));
+}
+
 __global__ void __launch_bounds__(256) hist_weights_kernel(const float *__restrict__ w, i64 n,
                                                            u32 *__restrict__ hist, int *status)
 {
-    __shared__ u32 s_h[4 * RADIX];
-    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x)
-        s_h[i] = 0;
+    __shared__ u32 s_h[HIST_WARPS][4 * RADIX];
+    for (int i = threadIdx.x; i < HIST_WARPS * 4 * RADIX; i += blockDim.x)
+        (&s_h[0][0])[i] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const i64 stride = (i64)gridDim.x * blockDim.x;
-    // every lane runs the same number of iterations so that warp votes are full
-    const i64 n_round = (n + 31) & ~(i64)31;
+    const int warp = threadIdx.x >> 5;
     bool nan_seen = false;
-    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n_round; i += stride) {
-        const bool valid = i < n;
-        float x = valid ? w[i] : 0.0f;
-        nan_seen |= (x != x);
-        u32 k = weight_key(x);
-        u32 k0 = __shfl_sync(0xFFFFFFFFu, k, 0);
-        u32 vm = __ballot_sync(0xFFFFFFFFu, valid);
-        bool uniform = __all_sync(0xFFFFFFFFu, k == k0) && vm == 0xFFFFFFFFu;
-        if (uniform) {
-            if (lane == 0) {
-#pragma unroll
-                for (int p = 0; p < 4; ++p)
-                    atomicAdd(&s_h[p * RADIX + ((k >> (8 * p)) & 255)], 32u);
-            }
-        } else if (valid) {
-#pragma unroll
-            for (int p = 0; p < 4; ++p)
-                atomicAdd(&s_h[p * RADIX + ((k >> (8 * p)) & 255)], 1u);
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 t0 = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((((uintptr_t)w) & 15) == 0) {
+        const float4 *w4 = (const float4 *)w;
+        const i64 n4 = n / 4;
+        // every lane of a warp runs the same iterations (full warp votes)
+        const i64 n4_round = (n4 + 31) & ~(i64)31;
+        for (i64 i = t0; i - (threadIdx.x & 31) < n4_round; i += stride) {
+            const bool valid = i < n4;
+            const float4 x = valid ? w4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            nan_seen |= (x.x != x.x) | (x.y != x.y) | (x.z != x.z) | (x.w != x.w);
+            hist_count(s_h, warp, weight_key(x.x), valid);
+            hist_count(s_h, warp, weight_key(x.y), valid);
+            hist_count(s_h, warp, weight_key(x.z), valid);
+            hist_count(s_h, warp, weight_key(x.w), valid);
+        }
+        // the last n % 4 weights
+        if (blockIdx.x == 0 && warp == 0) {
+            const i64 i = n4 * 4 + (threadIdx.x & 31);
+            const bool valid = i < n;
+            const float x = valid ? w[i] : 0.f;
+            nan_seen |= valid && (x != x);
+            hist_count(s_h, warp, weight_key(x), valid);
+        }
+    } else {
+        const i64 n_round = (n + 31) & ~(i64)31;
+        for (i64 i = t0; i - (threadIdx.x & 31) < n_round; i += stride) {
+            const bool valid = i < n;
+            const float x = valid ? w[i] : 0.f;
+            nan_seen |= (x != x);
+            hist_count(s_h, warp, weight_key(x), valid);
         }
     }
     if (nan_seen)
         set_status(status, PANDORA_ERR_NAN_WEIGHT);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) {
-        u32 c = s_h[i];
+        u32 c = 0;
+#pragma unroll
+        for (int k = 0; k < HIST_WARPS; ++k)
+            c += s_h[k][i];
         if (c)
             atomicAdd(hist + i, c);
     }
@@ -406,8 +440,8 @@ void launch_hist_weights(const float *w, i64 n, u32 *hist, int *status, cudaStre
     if (n <= 0)
         return;
     i64 blocks = (n + 256 * 16 - 1) / (256 * 16);
-    if (blocks > 152 * 8)
-        blocks = 152 * 8;
+    if (blocks > 152 * 4)
+        blocks = 152 * 4;
     hist_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(w, n, hist, status);
 }
 
