@@ -57,7 +57,8 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(s) <= lib_m for s in srcs):
             return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp] + srcs + ["-lm"]
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp] + srcs + \
+        ["-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +78,8 @@ def _load():
             lib.oracle_dendrogram_batched.restype = ctypes.c_int
             lib.oracle_edge_order.argtypes = [p, i64, p]
             lib.oracle_edge_order.restype = ctypes.c_int
+            lib.oracle_dendrogram_threads.argtypes = [p, p, p, i64, p, p, ctypes.c_int]
+            lib.oracle_dendrogram_threads.restype = ctypes.c_int
             lib.cartesian_path_dendrogram.argtypes = [p, p, i64, p, p]
             lib.cartesian_path_dendrogram.restype = ctypes.c_int
             _lib = lib
@@ -110,6 +113,24 @@ def dendrogram(u, v, w, check: bool = True):
     if st != OK:
         raise OracleError(st)
     return ep, vp
+
+
+def dendrogram_threads(u, v, w, n_threads: int):
+    """The same dendrogram with the edge sort on ``n_threads`` threads and the
+    union-find pass sequential (the all-core timing mode); raises
+    ``OracleError``."""
+    lib = _load()
+    u = _as(u, np.int32)
+    v = _as(v, np.int32)
+    w = _as(w, np.float32)
+    m = int(w.shape[0])
+    ep = np.empty(max(m, 1), np.int32)
+    vp = np.empty(m + 1, np.int32)
+    st = lib.oracle_dendrogram_threads(_ptr(u), _ptr(v), _ptr(w), m, _ptr(ep), _ptr(vp),
+                                       int(n_threads))
+    if st != OK:
+        raise OracleError(st)
+    return ep[:m], vp
 
 
 def dendrogram_batched(u, v, w, edge_offsets, check: bool = True):

@@ -31,6 +31,7 @@
  * "parity unpinned".
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -60,14 +61,11 @@ static int lighter(const float *w, int32_t a, int32_t b)
     return a < b;
 }
 
-/* Top-down merge sort of edge indices by the order above. */
-static void merge_sort(int32_t *idx, int32_t *tmp, int64_t lo, int64_t hi, const float *w)
+/* Stable merge of the sorted runs idx[lo, mid) and idx[mid, hi) by the order
+ * above (on equal keys the left run goes first). */
+static void merge_runs(int32_t *idx, int32_t *tmp, int64_t lo, int64_t mid, int64_t hi,
+                       const float *w)
 {
-    if (hi - lo < 2)
-        return;
-    int64_t mid = lo + (hi - lo) / 2;
-    merge_sort(idx, tmp, lo, mid, w);
-    merge_sort(idx, tmp, mid, hi, w);
     int64_t i = lo, j = mid, k = lo;
     while (i < mid && j < hi) {
         if (lighter(w, idx[j], idx[i]))
@@ -80,6 +78,17 @@ static void merge_sort(int32_t *idx, int32_t *tmp, int64_t lo, int64_t hi, const
     while (j < hi)
         tmp[k++] = idx[j++];
     memcpy(idx + lo, tmp + lo, (size_t)(hi - lo) * sizeof(int32_t));
+}
+
+/* Top-down merge sort of edge indices by the order above. */
+static void merge_sort(int32_t *idx, int32_t *tmp, int64_t lo, int64_t hi, const float *w)
+{
+    if (hi - lo < 2)
+        return;
+    int64_t mid = lo + (hi - lo) / 2;
+    merge_sort(idx, tmp, lo, mid, w);
+    merge_sort(idx, tmp, mid, hi, w);
+    merge_runs(idx, tmp, lo, mid, hi, w);
 }
 
 /* Union-find root with path halving. */
@@ -114,13 +123,108 @@ int oracle_edge_order(const float *w, int64_t n_edges, int32_t *order)
 }
 
 /*
+ * The same order computed by several threads (the all-core timing mode, which
+ * mirrors a parallel sort followed by a sequential union-find): the index
+ * array is cut into n_threads runs, each run is merge-sorted by its own
+ * thread, and the runs are merged pairwise, the merges of one round in
+ * parallel.  Every merge is the stable merge above, so the result is the same
+ * permutation as oracle_edge_order's (the order is total).
+ */
+struct sort_job {
+    int32_t *idx, *tmp;
+    int64_t lo, mid, hi;
+    const float *w;
+};
+
+static void *sort_run(void *arg)
+{
+    struct sort_job *j = (struct sort_job *)arg;
+    merge_sort(j->idx, j->tmp, j->lo, j->hi, j->w);
+    return NULL;
+}
+
+static void *merge_job(void *arg)
+{
+    struct sort_job *j = (struct sort_job *)arg;
+    merge_runs(j->idx, j->tmp, j->lo, j->mid, j->hi, j->w);
+    return NULL;
+}
+
+int oracle_edge_order_threads(const float *w, int64_t n_edges, int32_t *order, int n_threads)
+{
+    if (n_threads <= 1 || n_edges < 2 * (int64_t)n_threads)
+        return oracle_edge_order(w, n_edges, order);
+    if (n_threads > 256)
+        n_threads = 256;
+    for (int64_t e = 0; e < n_edges; ++e)
+        if (isnan(w[e]))
+            return ORACLE_ERR_NAN_WEIGHT;
+    int32_t *tmp = (int32_t *)malloc((size_t)n_edges * sizeof(int32_t));
+    if (!tmp)
+        return ORACLE_ERR_OUT_OF_MEMORY;
+    for (int64_t e = 0; e < n_edges; ++e)
+        order[e] = (int32_t)e;
+    int64_t bound[257];
+    for (int t = 0; t <= n_threads; ++t)
+        bound[t] = n_edges * t / n_threads;
+    struct sort_job jobs[256];
+    pthread_t th[256];
+    int status = ORACLE_OK;
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t] = (struct sort_job){order, tmp, bound[t], bound[t], bound[t + 1], w};
+        if (pthread_create(&th[t], NULL, sort_run, &jobs[t]) != 0) {
+            sort_run(&jobs[t]);
+            th[t] = 0;
+        }
+    }
+    for (int t = 0; t < n_threads; ++t)
+        if (th[t])
+            pthread_join(th[t], NULL);
+    /* pairwise merges: after round r, runs of 2^(r+1) original runs are sorted */
+    for (int width = 1; width < n_threads; width *= 2) {
+        int n_jobs = 0;
+        for (int t = 0; t + width < n_threads; t += 2 * width) {
+            int hi = t + 2 * width < n_threads ? t + 2 * width : n_threads;
+            jobs[n_jobs] = (struct sort_job){order, tmp, bound[t], bound[t + width], bound[hi], w};
+            if (pthread_create(&th[n_jobs], NULL, merge_job, &jobs[n_jobs]) != 0) {
+                merge_job(&jobs[n_jobs]);
+                th[n_jobs] = 0;
+            }
+            ++n_jobs;
+        }
+        for (int k = 0; k < n_jobs; ++k)
+            if (th[k])
+                pthread_join(th[k], NULL);
+    }
+    free(tmp);
+    return status;
+}
+
+/*
  * Dendrogram of one tree with n_edges edges and n_edges + 1 vertices.
  * u, v: endpoints in [0, n_edges]; w: weights; all arrays host memory owned
  * by the caller.  Returns 0 or an error code; on error the outputs are
  * unspecified.
  */
+static int dendrogram_impl(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                           int32_t *edge_parent, int32_t *vertex_parent, int n_threads);
+
 int oracle_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
                       int32_t *edge_parent, int32_t *vertex_parent)
+{
+    return dendrogram_impl(u, v, w, n_edges, edge_parent, vertex_parent, 1);
+}
+
+/* The same dendrogram with the sort on n_threads threads (timing mode). */
+int oracle_dendrogram_threads(const int32_t *u, const int32_t *v, const float *w,
+                              int64_t n_edges, int32_t *edge_parent, int32_t *vertex_parent,
+                              int n_threads)
+{
+    return dendrogram_impl(u, v, w, n_edges, edge_parent, vertex_parent, n_threads);
+}
+
+static int dendrogram_impl(const int32_t *u, const int32_t *v, const float *w, int64_t n_edges,
+                           int32_t *edge_parent, int32_t *vertex_parent, int n_threads)
 {
     if (n_edges < 0 || n_edges >= INT32_MAX || !vertex_parent)
         return ORACLE_ERR_INVALID_ARGUMENT;
@@ -154,7 +258,7 @@ int oracle_dendrogram(const int32_t *u, const int32_t *v, const float *w, int64_
         status = ORACLE_ERR_OUT_OF_MEMORY;
         goto done;
     }
-    status = oracle_edge_order(w, n_edges, order);
+    status = oracle_edge_order_threads(w, n_edges, order, n_threads);
     if (status != ORACLE_OK)
         goto done;
 

@@ -22,8 +22,12 @@ def test_reference_arm_json_line():
         assert k in d, k
     assert d["impl"] == "reference"
     assert d["unit"] == "edges/s" and d["value"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
-    assert d["config"]["workload"] == "rrt_1e8"
+    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    # the line names the sample it timed, not the full-size workload
+    assert d["config"]["workload"] == "rrt_1e8_sample_n10000000"
+    assert d["config"]["n_edges"] == 10_000_000 - 1
+    assert d["config"]["sample_of"].startswith("rrt_1e8")
 
 
 def test_structure_check_accepts_dendrograms_and_rejects_corruptions():

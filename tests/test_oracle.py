@@ -202,6 +202,25 @@ def test_single_vertex_and_single_edge():
     assert list(ep) == [-1] and list(vp) == [0, 0]
 
 
+@pytest.mark.parametrize("threads", [2, 3, 8, 16])
+def test_threaded_sort_mode_equals_single_thread(threads):
+    """The all-core timing mode (edge sort on several threads) gives the same
+    dendrogram as the single-threaded oracle: ties across run boundaries,
+    signed zeros and a tree smaller than the thread count included."""
+    cases = [inputs.rrt(50_000, 7), inputs.path(20_000, 3, kind="random"),
+             inputs.star(5_000, 1), inputs.rrt(5, 2)]
+    heavy = inputs.rrt(30_000, 9)
+    cases.append(inputs.with_weights(heavy, (np.arange(heavy.m) % 7).astype(np.float32)))
+    zeros = inputs.rrt(10_000, 4)
+    cases.append(inputs.with_weights(
+        zeros, np.where(np.arange(zeros.m) % 3 == 0, -0.0, 0.0).astype(np.float32)))
+    for t in cases:
+        a = oracle.dendrogram(t.u, t.v, t.w)
+        b = oracle.dendrogram_threads(t.u, t.v, t.w, threads)
+        _eq(a[0], b[0])
+        _eq(a[1], b[1])
+
+
 def test_batched_equals_per_tree():
     b = inputs.batch(12, 2, 3000, seed=4)
     ep, vp = oracle.dendrogram_batched(b.u, b.v, b.w, b.edge_offsets)

@@ -41,8 +41,8 @@ def _build(tmp_path, name, text):
     src = tmp_path / f"{name}.c"
     lib = tmp_path / f"{name}.so"
     src.write_text(text)
-    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-o", str(lib), str(src),
-                    "-lm"], check=True)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", str(lib),
+                    str(src), "-lm", "-lpthread"], check=True)
     so = ctypes.CDLL(str(lib))
     so.oracle_dendrogram.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64] + \
         [ctypes.c_void_p] * 2

@@ -6,18 +6,28 @@ the device up front), or they run a latency-critical loop in which
 cudaMalloc/cudaFree would synchronise the device.  For them the library has
 one entry point whose scratch is a fixed array in its device image.  These
 tests call it through the C ABI and require the same outputs as
-pandora_dendrogram (exact equality: the outputs are integers) on two calls in
-a row, the second smaller than the first so that contents left behind by the
-first call cannot leak into the second.
+pandora_dendrogram and as the CPU oracle (exact equality: the outputs are
+integers) on two calls in a row, the second smaller than the first so that
+contents left behind by the first call cannot leak into the second, and they
+check in a fresh process that the calls leave the device's free memory
+unchanged (nothing is allocated, not even from the library's pool).
 
-This file is collected last on purpose (see the file name).
+The file name makes pytest collect it last: should it fail, a run that stops
+at the first failure (-x) has already run every other test.
 """
 import ctypes
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2401_06089_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -61,6 +71,53 @@ def test_noalloc_matches_pandora_dendrogram_on_two_calls(lib):
         rep, rvp = pd.dendrogram(u, v, w)
         np.testing.assert_array_equal(ep, rep.cpu().numpy())
         np.testing.assert_array_equal(vp, rvp.cpu().numpy())
+        oep, ovp = oracle.dendrogram(t.u, t.v, t.w)
+        np.testing.assert_array_equal(ep, oep)
+        np.testing.assert_array_equal(vp, ovp)
+
+
+_FRESH = r"""
+import ctypes, json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_2401_06089_gb300 as pd
+from paper_2401_06089_gb300 import inputs
+lib = pd.load_library()
+P = ctypes.c_void_p
+lib.pandora_dendrogram_noalloc.argtypes = [P, P, P, ctypes.c_int64, P, P, P]
+dev = torch.device("cuda")
+trees = [inputs.rrt(200000, 31), inputs.rrt(3000, 32)]
+bufs = []
+for t in trees:
+    bufs.append([torch.from_numpy(t.u).to(dev), torch.from_numpy(t.v).to(dev),
+                 torch.from_numpy(t.w).to(dev), torch.empty(t.m, dtype=torch.int32, device=dev),
+                 torch.empty(t.m + 1, dtype=torch.int32, device=dev)])
+# load the library's kernels and start its runtime through a call that takes
+# a caller workspace (no allocation either)
+t = trees[1]
+b = bufs[1]
+ws = torch.empty(pd.workspace_size(t.m), dtype=torch.uint8, device=dev)
+pd.dendrogram_async(b[0], b[1], b[2], ws, (b[3], b[4]))
+torch.cuda.synchronize()
+stream = P(torch.cuda.current_stream().cuda_stream)
+free = [torch.cuda.mem_get_info()[0]]
+for t, b in zip(trees, bufs):
+    st = lib.pandora_dendrogram_noalloc(*[P(x.data_ptr()) for x in b[:3]], t.m,
+                                        P(b[3].data_ptr()), P(b[4].data_ptr()), stream)
+    torch.cuda.synchronize()
+    free.append(torch.cuda.mem_get_info()[0])
+    assert st == 0, st
+print(json.dumps({"free": free}))
+"""
+
+
+def test_noalloc_allocates_nothing_in_a_fresh_process(lib):
+    env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
+    r = subprocess.run([sys.executable, "-c", _FRESH, ROOT], capture_output=True, text=True,
+                       timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    free = json.loads(r.stdout.strip().splitlines()[-1])["free"]
+    assert free[0] == free[1] == free[2], free
 
 
 def test_noalloc_rejects_inputs_above_the_limit(lib):
