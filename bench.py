@@ -32,6 +32,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MST edges/s to dendrogram on 1 GB300 + HBM roofline %; batched vs per-tree speedup"
+# points of the HDBSCAN-shaped tree timed in the default run (the host
+# generator takes minutes at the configuration's 4e6 points; --workload
+# hdbscan_4m times the full size)
+HDBSCAN_BENCH_POINTS = 250_000
+# vertices of the tree the reference arm (the CPU oracle) times per step
+REFERENCE_SAMPLE = 10_000_000
 UNIT = "edges/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -70,6 +76,12 @@ def parse_args():
                          "edge order, two children per edge, Eq. 1)")
     ap.add_argument("--async-api", action="store_true",
                     help="time pandora_dendrogram_async (worst-case level count, no host sync)")
+    ap.add_argument("--membench", action="store_true",
+                    help="only measure the random-access ceilings (pandora_membench) and print "
+                         "them as one JSON line")
+    ap.add_argument("--membench-bps", type=int, nargs="*", default=[4, 8, 16],
+                    help="blocks per SM of the --membench kernels")
+    ap.add_argument("--membench-reps", type=int, default=5)
     ap.add_argument("--flat", type=int, default=0, metavar="MCS",
                     help="also time HDBSCAN* flat clusters (pandora_hdbscan_labels) with this "
                          "min_cluster_size on the workload's dendrogram")
@@ -267,37 +279,199 @@ def dist_setup(args):
 
 
 def run_reference(args):
-    """The CPU oracle on a bounded sample of the workload (rank 0 only)."""
-    import numpy as np
+    """The CPU oracle (the reference arm of this benchmark: the paper ships no
+    code) on a bounded sample of the workload, rank 0 only.  Every step is one
+    oracle dendrogram of the same sample in the all-core mode (edge sort on
+    every host core, union-find on one), the setting of the paper's UnionFind
+    baseline (parallel sort, sequential union-find).  The sample, not the full
+    workload, is what the line's config names."""
     import oracle
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
     spec = WORKLOADS[args.workload]
-    n_sample = min(args.n or spec["n"], 1_000_000)
+    n_full = args.n or spec["n"]
+    n_sample = min(n_full, REFERENCE_SAMPLE)
     t = make_tree(spec, n_sample)
     oracle.build()
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.dendrogram(t.u, t.v, t.w)
+        oracle.dendrogram_threads(t.u, t.v, t.w, cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.dendrogram(t.u, t.v, t.w)
+        oracle.dendrogram_threads(t.u, t.v, t.w, cores)
         times.append(time.perf_counter() - t0)
     sec = sum(times) / len(times)
     value = t.m / sec
-    sample = f"{spec['family']} n={n_sample} seed={spec['seed']} (same generator), one thread"
+    sample = (f"{spec['family']} n={n_sample} seed={spec['seed']} (same generator), edge sort "
+              f"on {cores} threads, union-find on one")
+    config = config_of(args, spec)
+    if n_sample != n_full:
+        config["workload"] = f"{config['workload']}_sample_n{n_sample}"
+        config["n_vertices"] = n_sample
+        config["n_edges"] = n_sample - 1
+        config["sample_of"] = f"{args.workload} (n={n_full})"
+        config["l2"] = "host caches; the oracle runs on the CPU"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_of(args, spec),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_rrt_1e4(pd, torch, args, reps=200):
+    """Configuration rrt_1e4 (n = 10^4, seed 0): launch-bound; the blocking
+    call by wall clock, the asynchronous call and its CUDA-graph replay by
+    CUDA events on the launching stream."""
+    spec = WORKLOADS["rrt_1e4"]
+    t = make_tree(spec)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    u = torch.from_numpy(t.u).to(dev)
+    v = torch.from_numpy(t.v).to(dev)
+    w = torch.from_numpy(t.w).to(dev)
+    ws = torch.empty(pd.workspace_size(t.m), dtype=torch.uint8, device=dev)
+    ep = torch.empty(t.m, dtype=torch.int32, device=dev)
+    vp = torch.empty(t.m + 1, dtype=torch.int32, device=dev)
+    for _ in range(10):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    blocking_ms = (time.perf_counter() - t0) * 1e3 / reps
+    ref = (ep.clone(), vp.clone())
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    for _ in range(10):
+        pd.dendrogram_async(u, v, w, ws, (ep, vp))
+    a.record(stream)
+    for _ in range(reps):
+        pd.dendrogram_async(u, v, w, ws, (ep, vp))
+    b.record(stream)
+    b.synchronize()
+    async_ms = a.elapsed_time(b) / reps
+    pd.workspace_status(ws)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        pd.dendrogram_async(u, v, w, ws, (ep, vp))
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        pd.dendrogram_async(u, v, w, ws, (ep, vp))
+    for _ in range(10):
+        g.replay()
+    a.record(stream)
+    for _ in range(reps):
+        g.replay()
+    b.record(stream)
+    b.synchronize()
+    graph_ms = a.elapsed_time(b) / reps
+    pd.workspace_status(ws)
+    same = bool(torch.equal(ep, ref[0]) and torch.equal(vp, ref[1]))
+    return {"n_vertices": t.n, "seed": spec["seed"], "reps": reps,
+            "blocking_ms": blocking_ms, "async_ms": async_ms, "graph_ms": graph_ms,
+            "edges_per_s_blocking": t.m / (blocking_ms / 1e3),
+            "edges_per_s_graph": t.m / (graph_ms / 1e3),
+            "timing": "blocking: wall clock; async and graph: CUDA events on the stream",
+            "outputs_equal_across_apis": same}
+
+
+def summarize_batched(line):
+    keep = ("value", "unit", "ms_per_step", "per_tree_blocking_ms", "per_tree_async_ms",
+            "speedup_vs_per_tree_blocking", "speedup_vs_per_tree_async", "gpu_launches_per_step",
+            "forest_async_graph_ms", "blocking_kernel_ms", "structure", "clocks")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = {k: line["config"][k] for k in ("n_trees", "total_edges", "family", "mode")}
+    kern = line.get("blocking_kernels", {})
+    tot = sum((e["ms"] or 0.0) for e in kern.values()) or 1.0
+    out["blocking_kernel_share"] = {k: round((e["ms"] or 0.0) / tot, 4) for k, e in kern.items()}
+    return out
+
+
+def summarize_serving(line):
+    keep = ("value", "unit", "latency_ms", "saturated_edges_per_s",
+            "per_request_blocking_edges_per_s", "speedup_saturated_vs_per_request",
+            "max_batches_in_flight", "gpu_launches", "clocks")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = line["config"]
+    return out
+
+
+def measure_hdbscan(pd, torch, args, n_points=None, reps=20):
+    """Configuration hdbscan: the mutual-reachability spanning tree of 3-D
+    Gaussian-mixture points (minPts 16), generated on the host once (cached
+    under /tmp by size and seed), timed like the headline."""
+    import numpy as np
+    spec = WORKLOADS["hdbscan_4m"]
+    n = n_points or HDBSCAN_BENCH_POINTS
+    path = f"/tmp/pandora_hdbscan_{n}_{spec['seed']}.npz"
+    t0 = time.perf_counter()
+    if os.path.exists(path):
+        z = np.load(path)
+        hu, hv, hw = z["u"], z["v"], z["w"]
+    else:
+        t = make_tree(spec, n)
+        hu, hv, hw = t.u, t.v, t.w
+        np.savez(path, u=hu, v=hv, w=hw)
+    gen_s = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    u = torch.from_numpy(hu).to(dev)
+    v = torch.from_numpy(hv).to(dev)
+    w = torch.from_numpy(hw).to(dev)
+    m = int(hw.shape[0])
+    ws = torch.empty(pd.workspace_size(m), dtype=torch.uint8, device=dev)
+    ep = torch.empty(m, dtype=torch.int32, device=dev)
+    vp = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    st = dendrogram_structure(hu, hv, hw, ep.cpu().numpy(), vp.cpu().numpy())
+    return {"value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": reps,
+            "n_points": n, "min_pts": 16, "seed": spec["seed"],
+            "tree": "mutual-reachability spanning tree from the host generator",
+            "generation_s": gen_s, "structure_ok": st["ok"]}
+
+
+def cpu_baseline(spec, n_override=None, n_sample=10_000_000):
+    """The CPU oracle on a bounded sample of the workload: one thread, and the
+    all-core mode (sort on every host core, union-find sequential)."""
+    import oracle
+    oracle.build()
+    n_s = min(n_override or spec["n"], n_sample)
+    ts = make_tree(spec, n_s)
+    t0 = time.perf_counter()
+    oracle.dendrogram(ts.u, ts.v, ts.w)
+    sec1 = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.dendrogram_threads(ts.u, ts.v, ts.w, cores)
+    secn = time.perf_counter() - t0
+    return {"value": ts.m / sec1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{spec['family']} n={n_s} seed={spec['seed']} (same generator), "
+                      f"one thread, {sec1:.1f} s",
+            "all_cores": {"value": ts.m / secn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                          "sample": f"same sample, sort on {cores} threads and union-find on "
+                                    f"one, {secn:.1f} s"}}
 
 
 def config_of(args, spec):
@@ -325,6 +499,13 @@ def time_device(pd, torch, t, steps, warmup, profile=True):
 
 
 def run_batched(args):
+    world, rank, _ = dist_setup(args)
+    line = measure_batched(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_batched(args, n_trees=None, init_dist=True):
     """Batched workload: the planned batched call captured in a CUDA graph,
     against one call per tree on the same GPU.  With N ranks the batch has
     N * n_trees trees, sharded by whole trees (largest first to the least
@@ -335,14 +516,16 @@ def run_batched(args):
     import paper_2401_06089_gb300 as pd
     from paper_2401_06089_gb300 import inputs
     world, rank, local = dist_setup(args)
-    if world > 1:
+    if world > 1 and init_dist:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    elif world > 1:
+        import torch.distributed as dist
     else:
         dist = None
-    spec = WORKLOADS[args.workload]
-    n_trees = args.n or spec["n"]
+    spec = WORKLOADS["batched_4096"]
+    n_trees = n_trees or args.n or spec["n"]
     n_total = n_trees * world
     if world > 1:
         from paper_2401_06089_gb300.sharding import shard_trees
@@ -498,7 +681,7 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": args.workload, "n_trees": n_total, "total_edges": int(m_all),
+        "config": {"workload": "batched_4096", "n_trees": n_total, "total_edges": int(m_all),
                    "trees_per_gpu": n_trees,
                    "parallelism": ("one GPU" if world == 1 else
                                    f"{world} GPUs, trees sharded largest-first, no collective"),
@@ -522,13 +705,19 @@ def run_batched(args):
         "levels": bstats["level_edges"],
         "clocks": sampler.summary(),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
+    if dist and init_dist:
         dist.destroy_process_group()
+    return line
 
 
 def run_serving(args):
+    _, rank, _ = dist_setup(args)
+    line = measure_serving(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_serving(args, n_req=None):
     """Continuous batching under Poisson arrivals (p50/p99 latency, edges/s)
     against one blocking call per request on the same trace."""
     import numpy as np
@@ -583,7 +772,7 @@ def run_serving(args):
     per_req_wall = time.perf_counter() - t0
     per_req_rate = sum(r.m for r in reqs) / per_req_wall
     # Poisson arrivals at 70% of the saturated rate
-    n_req = args.n or spec["n"]
+    n_req = n_req or args.n or spec["n"]
     rate = 0.7 * sat / mean_m
     reqs, arr = trace(n_req + 200, rate, 12)
     gpu_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid).replace("GPU-", "")
@@ -616,12 +805,71 @@ def run_serving(args):
         "gpu_launches": serve_kernels,
         "clocks": sampler.summary(),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
+
+
+# random 4-/8-byte accesses over vertex-sized arrays (10^8 elements), the
+# access pattern of the level kernels; windows of 2^22 elements are the
+# pattern of a bucketed pass (a bucket that stays in L2)
+MEMBENCH_CASES = [
+    ("gather32", 10**8, 0), ("gather64", 10**8, 0), ("scatter32", 10**8, 0),
+    ("scatter64", 10**8, 0), ("atomicmin64", 10**8, 0), ("gather64", 10**8, 1 << 22),
+    ("atomicmin64", 10**8, 1 << 22), ("gather32", 10**7, 0), ("copy32", 10**8, 0),
+]
+
+
+def measure_random_access(torch, pd, n_access=1 << 27, reps=5, blocks_per_sm=8,
+                          cases=MEMBENCH_CASES):
+    """Accesses per second of each random-access kind (CUDA events on the
+    launching stream, mean of `reps` launches after one warm-up)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    out = []
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    for kind, n, window in cases:
+        width = 8 if kind.endswith("64") else 4
+        buf = torch.zeros(n, dtype=torch.int64 if width == 8 else torch.int32, device=dev)
+        if kind == "atomicmin64":
+            buf.fill_(-1)   # all ones: every atomic has something to lower at first
+        dst = torch.empty(n, dtype=torch.int32, device=dev) if kind == "copy32" else None
+        acc = n if kind == "copy32" else n_access
+        pd.membench(kind, buf, n_access=acc, window=window, dst=dst, sink=sink,
+                    blocks_per_sm=blocks_per_sm)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for r in range(reps):
+            pd.membench(kind, buf, n_access=acc, window=window, seed=r + 1, dst=dst, sink=sink,
+                        blocks_per_sm=blocks_per_sm)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        moved = acc * (2 * width if kind == "copy32" else width)
+        out.append({"kind": kind, "elem_bytes": width, "array_bytes": n * width,
+                    "window_bytes": (window or n) * width, "accesses": acc, "ms": ms,
+                    "g_access_per_s": acc / ms / 1e6, "useful_gbs": moved / ms / 1e6})
+        del buf, dst
+    return out
+
+
+def run_membench(args):
+    import torch
+    import paper_2401_06089_gb300 as pd
+    pd.load_library()
+    res = {}
+    for bps in args.membench_bps:
+        res[f"bps{bps}"] = measure_random_access(torch, pd, reps=args.membench_reps,
+                                                 blocks_per_sm=bps)
+    peak, kind = load_peaks()
+    print(json.dumps({"metric": "random-access ceiling (pandora_membench)",
+                      "unit": "G accesses/s", "hbm_peak_gbs": peak, "peak_source": kind,
+                      "results": res}), flush=True)
 
 
 def main():
     args = parse_args()
+    if args.membench:
+        return run_membench(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
@@ -834,16 +1082,7 @@ def main():
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1) -------------------
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        import oracle
-        oracle.build()
-        n_s = min(args.n or spec["n"], 10_000_000)
-        ts = t if n_s == (args.n or spec["n"]) else make_tree(spec, n_s)
-        t0 = time.perf_counter()
-        oracle.dendrogram(ts.u, ts.v, ts.w)
-        sec = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": ts.m / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{spec['family']} n={n_s} seed={spec['seed']}, "
-                                          f"one thread, {sec:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline(spec, args.n)
     # ---- HDBSCAN* flat clusters on the same dendrogram (optional) ----------
     if args.flat and rank == 0:
         pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
@@ -868,6 +1107,14 @@ def main():
         gep, gvp = pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
         line["structure"] = dendrogram_structure(t.u, t.v, t.w, gep.cpu().numpy(),
                                                  gvp.cpu().numpy())
+    # ---- the other configurations, each as a sub-record -----------------
+    if not args.no_extra and args.workload == "rrt_1e8" and args.n is None:
+        line["rrt_1e4"] = measure_rrt_1e4(pd, torch, args)
+        line["batched_4096"] = summarize_batched(measure_batched(args, init_dist=False))
+        torch.cuda.empty_cache()
+        line["serving"] = summarize_serving(measure_serving(args))
+        torch.cuda.empty_cache()
+        line["hdbscan"] = measure_hdbscan(pd, torch, args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -809,16 +809,20 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
 // Blocks for n elements at per_block each, capped at PANDORA_LV_BPS blocks
 // per SM: every level kernel loops (grid-stride or over claimed tiles), so a
 // grid sized for a worst-case bound does not launch idle blocks by the
-// million.  The level kernels are bound by random DRAM reads, which more
-// blocks in flight do not speed up; on a 10^8-vertex path the union-find
-// part ran 20% faster at 4 blocks per SM than at 16.
+// million.  The level kernels are bound by random DRAM reads: 8 blocks per SM
+// measured 0.2 ms faster than 4 over all levels of a 10^8-edge random
+// recursive tree, while the union-find part ran 20% faster at 4 blocks per SM
+// than at 16 on a 10^8-vertex path (PANDORA_UF_BPS).
 #ifndef PANDORA_LV_BPS
-#define PANDORA_LV_BPS 4
+#define PANDORA_LV_BPS 8
 #endif
-static unsigned grid_for(i64 n, int per_block)
+#ifndef PANDORA_UF_BPS
+#define PANDORA_UF_BPS 4
+#endif
+static unsigned grid_for(i64 n, int per_block, int bps = PANDORA_LV_BPS)
 {
     i64 b = (n + per_block - 1) / per_block;
-    const i64 cap = 152 * PANDORA_LV_BPS;
+    const i64 cap = 152 * bps;
     if (b > cap)
         b = cap;
     return (unsigned)(b < 1 ? 1 : b);
@@ -898,12 +902,13 @@ void launch_compress(const LevelParams &p, cudaStream_t s)
     else
         compress_walk_kernel<false><<<blocks, 256, 0, s>>>(p);
     // the union-find part exits at once when the deep list is empty
-    uf_union_kernel<<<blocks, 256, 0, s>>>(p);
-    uf_tops_kernel<<<blocks, 256, 0, s>>>(p);
+    const unsigned uf_blocks = grid_for(p.n_grid, 256, PANDORA_UF_BPS);
+    uf_union_kernel<<<uf_blocks, 256, 0, s>>>(p);
+    uf_tops_kernel<<<uf_blocks, 256, 0, s>>>(p);
     if (p.level == 0)
-        uf_finish_kernel<true><<<blocks, 256, 0, s>>>(p);
+        uf_finish_kernel<true><<<uf_blocks, 256, 0, s>>>(p);
     else
-        uf_finish_kernel<false><<<blocks, 256, 0, s>>>(p);
+        uf_finish_kernel<false><<<uf_blocks, 256, 0, s>>>(p);
 }
 
 void launch_compact(const LevelParams &p, cudaStream_t s)
