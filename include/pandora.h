@@ -68,10 +68,12 @@ typedef enum pandora_status {
                                            n_vertices above PANDORA_FLAT_MAX_VERTICES */
     PANDORA_ERR_BAD_WEIGHT = 11,        /* flat clusters: a weight is not positive and
                                            finite (lambda = 1 / w is needed) */
-    PANDORA_ERR_NOT_A_DENDROGRAM = 12   /* flat clusters: the parent arrays are not a
+    PANDORA_ERR_NOT_A_DENDROGRAM = 12,  /* flat clusters: the parent arrays are not a
                                            binary tree with one root in which every
                                            edge comes after its children in the
                                            (weight, index) order */
+    PANDORA_ERR_BAD_POINT = 13          /* spanning tree of points: a coordinate is
+                                           not finite */
 } pandora_status;
 
 /* Per-call statistics (optional output of the *_ws entry points). */
@@ -210,6 +212,23 @@ int pandora_dendrogram_batched_planned(const int32_t *u, const int32_t *v, const
 /* Waits for `stream` and returns the device status word of the last call
  * that used `workspace` (PANDORA_OK when it found no error). */
 int pandora_workspace_status(const void *workspace, void *stream);
+
+/*
+ * Failure reporting of the bounded device loops (process-wide, host only;
+ * the paper has no counterpart).  Every wait of a kernel on another block
+ * (the single-pass scans' and sorts' look-back) and every union-find loop of
+ * the contraction (Section 3.2) is bounded; a loop that runs into its bound
+ * records PANDORA_ERR_ITERATION_LIMIT in the call's status word, which the
+ * blocking entry points return and pandora_workspace_status reads.  This
+ * setter makes those loops record that status as soon as they run longer
+ * than `spins` iterations, WITHOUT cutting them short: the results stay
+ * exact, only the status reports the long loop.  It exists so that a test
+ * can drive the reporting path on a real GPU without faulting or hanging
+ * it.  spins < 0 restores the default (report only at the hard bound).
+ * Calls already enqueued keep the limit they were enqueued with.  Returns
+ * PANDORA_OK.
+ */
+int pandora_set_wait_report_limit(int64_t spins);
 
 /*
  * Allocation-free variant of pandora_dendrogram.  The paper has no

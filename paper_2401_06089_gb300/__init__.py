@@ -22,7 +22,9 @@ from ._binding import (  # noqa: F401
     profile_start,
     load_library,
     membench,
+    mr_emst,
     set_tuning,
+    set_wait_report_limit,
     status_string,
     workspace_size,
     workspace_status,

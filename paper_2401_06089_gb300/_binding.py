@@ -33,6 +33,7 @@ STATUS_NAMES = {
     10: "PANDORA_ERR_SIZE_LIMIT",
     11: "PANDORA_ERR_BAD_WEIGHT",
     12: "PANDORA_ERR_NOT_A_DENDROGRAM",
+    13: "PANDORA_ERR_BAD_POINT",
 }
 
 FLAT_MAX_VERTICES = 536870912   # PANDORA_FLAT_MAX_VERTICES
@@ -107,13 +108,16 @@ def load_library():
                                                ctypes.POINTER(I64), P]
         lib.pandora_membench.argtypes = [ctypes.c_int, P, P, P, I64, I64, I64, ctypes.c_uint64,
                                          ctypes.c_int, P]
+        lib.pandora_mr_emst.argtypes = [P, I64, ctypes.c_int32, P, P, P, P, P]
+        lib.pandora_set_wait_report_limit.argtypes = [I64]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
                      "pandora_dendrogram_async", "pandora_dendrogram_batched_async",
                      "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
                      "pandora_dendrogram_batched_planned", "pandora_dendrogram_host",
-                     "pandora_hdbscan_labels", "pandora_membench"):
+                     "pandora_hdbscan_labels", "pandora_membench", "pandora_mr_emst",
+                     "pandora_set_wait_report_limit"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     _apply_default_tuning()
@@ -514,3 +518,41 @@ def membench(kind: str, buf, *, n_access: int, window: int = 0, seed: int = 0,
                               int(blocks_per_sm), stream)
     if st:
         raise PandoraError(st, "pandora_membench")
+
+
+EMST_MAX_MIN_PTS = 32   # PANDORA_EMST_MAX_MIN_PTS
+
+
+def mr_emst(points, min_pts: int, *, core: bool = False):
+    """Mutual-reachability minimum spanning tree of 3-D points
+    (``pandora_mr_emst``): points is a float32 CUDA tensor [n, 3]; returns
+    int32 u, v and float32 w of the n - 1 tree edges (u < v), and with
+    ``core`` also the float32 squared core distance of every point."""
+    torch = _torch()
+    if not isinstance(points, torch.Tensor) or not points.is_cuda:
+        raise ValueError("points must be a CUDA tensor (there is no CPU path)")
+    if points.dtype != torch.float32 or points.dim() != 2 or points.shape[1] != 3 or \
+            not points.is_contiguous():
+        raise ValueError("points must be a contiguous float32 tensor of shape [n, 3]")
+    n = points.shape[0]
+    dev = points.device
+    u = torch.empty(max(n - 1, 0), dtype=torch.int32, device=dev)
+    v = torch.empty(max(n - 1, 0), dtype=torch.int32, device=dev)
+    w = torch.empty(max(n - 1, 0), dtype=torch.float32, device=dev)
+    cs = torch.empty(n, dtype=torch.float32, device=dev) if core else None
+    lib = load_library()
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_mr_emst(_ptr(points), n, int(min_pts), _ptr(u), _ptr(v), _ptr(w),
+                                 _ptr(cs), stream)
+    if st:
+        raise PandoraError(st, "pandora_mr_emst")
+    return (u, v, w, cs) if core else (u, v, w)
+
+
+def set_wait_report_limit(spins: int) -> None:
+    """Make the bounded device loops (look-back waits, union-find loops)
+    report PANDORA_ERR_ITERATION_LIMIT once they run longer than ``spins``
+    iterations, without cutting them short (``pandora_set_wait_report_limit``;
+    negative: the default)."""
+    load_library().pandora_set_wait_report_limit(int(spins))

@@ -104,9 +104,14 @@ constexpr u64 LB_VAL = (1ull << 62) - 1;
 
 // Decoupled look-back for one counter (Merrill & Garland).  Called by ONE
 // thread of the block; returns the exclusive prefix of `aggregate` over all
-// earlier tiles.  Waits are bounded: on timeout the status word records
-// PANDORA_ERR_ITERATION_LIMIT and the partial prefix is returned.
-__device__ __forceinline__ u64 lookback_exclusive(u64 *lb, u32 tile, u64 aggregate, int *status)
+// earlier tiles.  Waits are bounded: a wait longer than `report` spins
+// records PANDORA_ERR_ITERATION_LIMIT and goes on (pandora_set_wait_report_limit
+// lowers `report` so that tests can see the status without cutting a wait
+// short); after SPIN_LIMIT spins the status is recorded and the partial
+// prefix is returned, which can only move this tile's outputs to lower,
+// still valid positions.
+__device__ __forceinline__ u64 lookback_exclusive(u64 *lb, u32 tile, u64 aggregate, int *status,
+                                                  u32 report = SPIN_LIMIT)
 {
     if (tile == 0) {
         st_relaxed(lb, LB_INC | aggregate);
@@ -120,7 +125,10 @@ __device__ __forceinline__ u64 lookback_exclusive(u64 *lb, u32 tile, u64 aggrega
         u64 s = ld_relaxed(lb + j);
         u64 f = s & ~LB_VAL;
         if (f == 0) {
-            if (++spins > SPIN_LIMIT) {
+            ++spins;
+            if (spins == report + 1u)
+                set_status(status, PANDORA_ERR_ITERATION_LIMIT);
+            if (spins > SPIN_LIMIT) {
                 set_status(status, PANDORA_ERR_ITERATION_LIMIT);
                 break;
             }
@@ -185,7 +193,8 @@ __device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity)
 // Bounded wait for phase `parity` of `bar`.  On timeout the status word
 // records PANDORA_ERR_ITERATION_LIMIT and the wait goes on, bounded again,
 // so that the block never leaves while its own copies are still landing in
-// its shared memory; returns false if both bounds ran out.
+// its shared memory; returns false if both bounds ran out (the status then
+// already says so, and the call's outputs are unspecified).
 __device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity, int *status)
 {
     for (u32 i = 0; i < SPIN_LIMIT; ++i)

@@ -58,6 +58,7 @@ struct OnesweepParams {
     i64 n_vertices;
     const i64 *edge_off;   // OS_FOREST
     i64 n_trees;
+    u32 report_limit = SPIN_LIMIT;   // look-back waits longer than this record ITERATION_LIMIT
 };
 
 __host__ __device__ inline i64 onesweep_tiles(i64 n) { return (n + OS_TILE - 1) / OS_TILE; }
@@ -65,6 +66,8 @@ __host__ __device__ inline i64 onesweep_tiles(i64 n) { return (n + OS_TILE - 1) 
 void launch_hist_weights(const float *w, i64 n, u32 *hist /*[4][256]*/, int *status,
                          cudaStream_t s);
 void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s);
+// digit histograms of 32-bit keys for the four 8-bit passes ([4][256], added to)
+void launch_hist_keys(const u32 *keys, i64 n, u32 *hist, cudaStream_t s);
 // base[r][d] = sum of hist[r][d'] over d' < d, for `rows` rows of 256
 void launch_hist_scan(const u32 *hist, u32 *base, int rows, cudaStream_t s);
 
@@ -148,7 +151,13 @@ struct LevelParams {
     // Section 3.2).  A single tree uses the level's root count instead.
     u32 *tree_roots;       // [n_trees]
     i32 *tree_root_id;     // [n_trees]
+    // look-back waits and union-find loops running longer than this record
+    // PANDORA_ERR_ITERATION_LIMIT (and go on to their hard bounds)
+    u32 report_limit = SPIN_LIMIT;
 };
+
+// Process-wide report limit of the bounded device loops (host side).
+u32 wait_report_limit();
 
 __host__ __device__ inline i64 eflag_words(i64 m) { return (m + 15) / 16; }
 

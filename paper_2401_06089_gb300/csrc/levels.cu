@@ -42,7 +42,7 @@ static_assert(LV_ITEMS * LV_WARPS == 64, "scan helper assumes 64 (item, warp) sl
 // Returns the tile total in *tile_total.
 __device__ __forceinline__ void tile_rank(const bool (&flag)[LV_ITEMS], u32 (&rank)[LV_ITEMS],
                                           u32 tile, u64 *lb, int *status, u64 *base_out,
-                                          u32 *tile_total)
+                                          u32 *tile_total, u32 report)
 {
     __shared__ u32 s_cnt[LV_ITEMS * LV_WARPS];
     __shared__ u64 s_base;
@@ -71,7 +71,7 @@ __device__ __forceinline__ void tile_rank(const bool (&flag)[LV_ITEMS], u32 (&ra
         s_cnt[2 * lane + 1] = excl + c0;
         const u32 total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         if (lane == 0) {
-            s_base = lookback_exclusive(lb, tile, total, status);
+            s_base = lookback_exclusive(lb, tile, total, status, report);
             s_total = total;
         }
     }
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
         u32 rank[LV_ITEMS];
         u64 base;
         u32 total;
-        tile_rank(root, rank, tile, p.lb, p.status, &base, &total);
+        tile_rank(root, rank, tile, p.lb, p.status, &base, &total, p.report_limit);
 #pragma unroll
         for (int it = 0; it < LV_ITEMS; ++it) {
             const i64 x = tile_base + it * LV_THREADS + threadIdx.x;
@@ -588,7 +588,10 @@ __global__ void __launch_bounds__(256) compress_walk_kernel(const LevelParams p)
     }
 }
 
-__device__ __forceinline__ i32 uf_find(i32 *uf, i32 a, int *status, i64 bound)
+// Root of a's union-find tree with path halving.  More than `report` steps
+// record PANDORA_ERR_ITERATION_LIMIT (the find goes on); more than `bound`
+// steps record it and stop at the ancestor reached.
+__device__ __forceinline__ i32 uf_find(i32 *uf, i32 a, int *status, i64 bound, u32 report)
 {
     i64 iter = 0;
     for (;;) {
@@ -599,7 +602,10 @@ __device__ __forceinline__ i32 uf_find(i32 *uf, i32 a, int *status, i64 bound)
         if (ga != pa)
             st_volatile(uf + a, ga);   // path halving (benign race: ga is an ancestor)
         a = ga;
-        if (++iter > bound) {
+        ++iter;
+        if (iter == (i64)report + 1)
+            set_status(status, PANDORA_ERR_ITERATION_LIMIT);
+        if (iter > bound) {
             set_status(status, PANDORA_ERR_ITERATION_LIMIT);
             return a;
         }
@@ -645,8 +651,8 @@ __global__ void __launch_bounds__(256) uf_union_kernel(const LevelParams p)
         // other one (see uf_priority)
         i32 a = x, b = y;
         for (i64 iter = 0;; ++iter) {
-            a = uf_find(p.uf, a, p.status, bound);
-            b = uf_find(p.uf, b, p.status, bound);
+            a = uf_find(p.uf, a, p.status, bound, p.report_limit);
+            b = uf_find(p.uf, b, p.status, bound, p.report_limit);
             if (a == b)
                 break;
             if (uf_priority(a) > uf_priority(b)) {
@@ -658,6 +664,8 @@ __global__ void __launch_bounds__(256) uf_union_kernel(const LevelParams p)
             if (old == a)
                 break;
             a = old;
+            if (iter == (i64)p.report_limit)
+                set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
             if (iter > bound) {
                 set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
                 break;
@@ -678,7 +686,7 @@ __global__ void __launch_bounds__(256) uf_tops_kernel(const LevelParams p)
         const i32 y = ld_volatile(p.ptr + x);
         const i32 py = ld_volatile(p.ptr + y);
         if (py < 0)
-            p.root_of[uf_find(p.uf, x, p.status, bound)] = ~py;
+            p.root_of[uf_find(p.uf, x, p.status, bound, p.report_limit)] = ~py;
     }
 }
 
@@ -692,7 +700,8 @@ __global__ void __launch_bounds__(256) uf_finish_kernel(const LevelParams p)
     for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nd;
          k += (i64)gridDim.x * blockDim.x) {
         const i32 x = p.deep[k];
-        write_supervertex<LEVEL0>(p, x, p.root_of[uf_find(p.uf, x, p.status, bound)]);
+        write_supervertex<LEVEL0>(p, x,
+                                  p.root_of[uf_find(p.uf, x, p.status, bound, p.report_limit)]);
     }
 }
 
@@ -777,7 +786,8 @@ __global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p
         u32 rank[LV_ITEMS];
         u64 base;
         u32 total;
-        tile_rank(alpha, rank, tile, p.lb + level_tiles(p.n_grid) + 1, p.status, &base, &total);
+        tile_rank(alpha, rank, tile, p.lb + level_tiles(p.n_grid) + 1, p.status, &base, &total,
+                  p.report_limit);
 #pragma unroll
         for (int it = 0; it < LV_ITEMS; ++it) {
             if (alpha[it]) {

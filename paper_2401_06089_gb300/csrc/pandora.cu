@@ -8,6 +8,7 @@
 // Between levels the host reads back two counters (the next level's edges and
 // vertices) to size the next launches; nothing else leaves the device.
 #include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstring>
 #include <map>
@@ -326,6 +327,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     int *status = &ctrl->status;
 
     CallTimer timer(s, blocking);
+    const u32 report = wait_report_limit();
     HostCounters h{};
     h.lvl_m[0] = (u64)M;
     h.lvl_n[0] = (u64)N;
@@ -380,6 +382,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     for (size_t k = 0; k < passes.size(); ++k) {
         const bool first = k == 0, last = k + 1 == passes.size();
         OnesweepParams P{};
+        P.report_limit = report;
         P.n = M;
         P.shift = 8 * passes[k];
         P.hist = ctrl->hist1[passes[k]];
@@ -475,6 +478,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
             break;
         }
         LevelParams P{};
+        P.report_limit = report;
         P.level = l;
         P.d_m = &ctrl->lvl_m[l];
         P.d_n = &ctrl->lvl_n[l];
@@ -646,6 +650,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     const u32 *sk = keysA, *sv = perm;
     for (size_t k = 0; k < passes2.size(); ++k) {
         OnesweepParams P{};
+        P.report_limit = report;
         P.n = M;
         P.shift = 8 * passes2[k];
         P.hist = ctrl->hist2[passes2[k]];
@@ -711,6 +716,8 @@ Tuning &tuning()
     static Tuning t;
     return t;
 }
+std::atomic<u32> g_report_limit{SPIN_LIMIT};
+
 pandora_tuning tuning_snapshot()
 {
     Tuning &t = tuning();
@@ -1119,6 +1126,10 @@ cudaMemPool_t flat_pool(int dev) { return library_pool(dev); }
 
 using namespace pandora;
 
+namespace pandora {
+u32 wait_report_limit() { return g_report_limit.load(); }
+}  // namespace pandora
+
 extern "C" {
 
 int pandora_workspace_size(int64_t total_edges, int64_t n_trees, size_t *bytes)
@@ -1323,6 +1334,14 @@ const char *pandora_status_string(int status)
     case PANDORA_ERR_BAD_POINT: return "point coordinate not finite";
     default: return "unknown status";
     }
+}
+
+int pandora_set_wait_report_limit(int64_t spins)
+{
+    pandora::g_report_limit.store(spins < 0 || spins >= (int64_t)pandora::SPIN_LIMIT
+                                      ? pandora::SPIN_LIMIT
+                                      : (pandora::u32)spins);
+    return PANDORA_OK;
 }
 
 int pandora_version(void) { return 100; }

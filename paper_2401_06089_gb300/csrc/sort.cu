@@ -136,6 +136,33 @@ __global__ void __launch_bounds__(256) hist_weights_kernel(const float *__restri
     }
 }
 
+// Digit histograms of 32-bit keys for all four passes (one read of the keys).
+__global__ void __launch_bounds__(256) hist_keys_kernel(const u32 *__restrict__ keys, i64 n,
+                                                        u32 *__restrict__ hist)
+{
+    __shared__ u32 s_h[HIST_WARPS][4 * RADIX];
+    for (int i = threadIdx.x; i < HIST_WARPS * 4 * RADIX; i += blockDim.x)
+        (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const i64 stride = (i64)gridDim.x * blockDim.x;
+    const i64 n_round = (n + 31) & ~(i64)31;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i - (threadIdx.x & 31) < n_round;
+         i += stride) {
+        const bool valid = i < n;
+        hist_count(s_h, warp, valid ? keys[i] : 0u, valid);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) {
+        u32 c = 0;
+#pragma unroll
+        for (int k = 0; k < HIST_WARPS; ++k)
+            c += s_h[k][i];
+        if (c)
+            atomicAdd(hist + i, c);
+    }
+}
+
 // Dynamic shared memory of one onesweep block: the input streams of the tile
 // as the TMA lands them (keys; values; u, v), one staging buffer for the
 // digit-ordered output, per-warp digit counts and the digit of each output
@@ -336,7 +363,10 @@ __global__ void __launch_bounds__(OS_THREADS, (FLAGS & OS_PAYLOAD_UV) ? OS_MIN_B
                     break;
                 j -= consumed;
                 if (consumed == 0) {
-                    if (++spins > SPIN_LIMIT) {
+                    ++spins;
+                    if (spins == p.report_limit + 1u)
+                        set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
+                    if (spins > SPIN_LIMIT) {
                         set_status(p.status, PANDORA_ERR_ITERATION_LIMIT);
                         break;
                     }
@@ -433,6 +463,16 @@ __global__ void __launch_bounds__(RADIX) hist_scan_kernel(const u32 *hist, u32 *
 void launch_hist_scan(const u32 *hist, u32 *base, int rows, cudaStream_t s)
 {
     hist_scan_kernel<<<rows, RADIX, 0, s>>>(hist, base);
+}
+
+void launch_hist_keys(const u32 *keys, i64 n, u32 *hist, cudaStream_t s)
+{
+    if (n <= 0)
+        return;
+    i64 blocks = (n + 256 * 16 - 1) / (256 * 16);
+    if (blocks > 152 * 4)
+        blocks = 152 * 4;
+    hist_keys_kernel<<<(unsigned)blocks, 256, 0, s>>>(keys, n, hist);
 }
 
 void launch_hist_weights(const float *w, i64 n, u32 *hist, int *status, cudaStream_t s)
