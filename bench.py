@@ -32,10 +32,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MST edges/s to dendrogram on 1 GB300 + HBM roofline %; batched vs per-tree speedup"
-# points of the HDBSCAN-shaped tree timed in the default run (the host
-# generator takes minutes at the configuration's 4e6 points; --workload
-# hdbscan_4m times the full size)
-HDBSCAN_BENCH_POINTS = 250_000
 # vertices of the tree the reference arm (the CPU oracle) times per step
 REFERENCE_SAMPLE = 10_000_000
 UNIT = "edges/s"
@@ -408,29 +404,27 @@ def summarize_serving(line):
     return out
 
 
-def measure_hdbscan(pd, torch, args, n_points=None, reps=20):
-    """Configuration hdbscan: the mutual-reachability spanning tree of 3-D
-    Gaussian-mixture points (minPts 16), generated on the host once (cached
-    under /tmp by size and seed), timed like the headline."""
+def measure_hdbscan(pd, torch, args, n_points=None, reps=20, mcs=16):
+    """Configuration hdbscan_4m end to end on the GPU: 4e6 points of the
+    32-component Gaussian mixture, their exact mutual-reachability minimum
+    spanning tree (minPts 16) by pandora_mr_emst, the dendrogram of that tree
+    (timed like the headline) and its HDBSCAN* flat clusters."""
     import numpy as np
+    from paper_2401_06089_gb300 import inputs
     spec = WORKLOADS["hdbscan_4m"]
-    n = n_points or HDBSCAN_BENCH_POINTS
-    path = f"/tmp/pandora_hdbscan_{n}_{spec['seed']}.npz"
-    t0 = time.perf_counter()
-    if os.path.exists(path):
-        z = np.load(path)
-        hu, hv, hw = z["u"], z["v"], z["w"]
-    else:
-        t = make_tree(spec, n)
-        hu, hv, hw = t.u, t.v, t.w
-        np.savez(path, u=hu, v=hv, w=hw)
-    gen_s = time.perf_counter() - t0
-    dev = torch.device("cuda", torch.cuda.current_device())
+    n = n_points or spec["n"]
+    pts = torch.from_numpy(inputs.gmm_points(n, spec["seed"]).astype(np.float32)).cuda()
+    dev = pts.device
     stream = torch.cuda.current_stream(dev)
-    u = torch.from_numpy(hu).to(dev)
-    v = torch.from_numpy(hv).to(dev)
-    w = torch.from_numpy(hw).to(dev)
-    m = int(hw.shape[0])
+    u, v, w = pd.mr_emst(pts, 16)   # warm-up
+    torch.cuda.synchronize()
+    emst_ms = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        u, v, w = pd.mr_emst(pts, 16)
+        torch.cuda.synchronize()
+        emst_ms.append((time.perf_counter() - t0) * 1e3)
+    m = u.numel()
     ws = torch.empty(pd.workspace_size(m), dtype=torch.uint8, device=dev)
     ep = torch.empty(m, dtype=torch.int32, device=dev)
     vp = torch.empty(m + 1, dtype=torch.int32, device=dev)
@@ -445,11 +439,29 @@ def measure_hdbscan(pd, torch, args, n_points=None, reps=20):
     b.record(stream)
     b.synchronize()
     ms = a.elapsed_time(b) / reps
-    st = dendrogram_structure(hu, hv, hw, ep.cpu().numpy(), vp.cpu().numpy())
+    labels = pd.hdbscan_labels(ep, vp, w, mcs)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(3):
+        labels = pd.hdbscan_labels(ep, vp, w, mcs)
+    b.record(stream)
+    b.synchronize()
+    flat_ms = a.elapsed_time(b) / 3
+    lab = labels.cpu().numpy()
+    st = dendrogram_structure(u.cpu().numpy(), v.cpu().numpy(), w.cpu().numpy(),
+                              ep.cpu().numpy(), vp.cpu().numpy())
+    emst = statistics.median(emst_ms)
     return {"value": m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": reps,
             "n_points": n, "min_pts": 16, "seed": spec["seed"],
-            "tree": "mutual-reachability spanning tree from the host generator",
-            "generation_s": gen_s, "structure_ok": st["ok"]}
+            "tree": "exact mutual-reachability minimum spanning tree (pandora_mr_emst, float32 "
+                    "reading), computed on the GPU",
+            "emst_ms": emst, "emst_points_per_s": n / (emst / 1e3),
+            "emst_timing": "wall clock around the blocking call, median of 3",
+            "flat_clusters": {"min_cluster_size": mcs, "ms_per_call": flat_ms,
+                              "clusters": int(lab.max()) + 1,
+                              "noise_fraction": float((lab < 0).mean())},
+            "pipeline_ms": emst + ms + flat_ms,
+            "structure_ok": st["ok"]}
 
 
 def cpu_baseline(spec, n_override=None, n_sample=10_000_000):
