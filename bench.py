@@ -75,6 +75,9 @@ def parse_args():
     ap.add_argument("--membench", action="store_true",
                     help="only measure the random-access ceilings (pandora_membench) and print "
                          "them as one JSON line")
+    ap.add_argument("--emst", type=int, default=0, metavar="POINTS",
+                    help="only time the mutual-reachability spanning tree (pandora_mr_emst) of "
+                         "this many Gaussian-mixture points and print one JSON line")
     ap.add_argument("--membench-bps", type=int, nargs="*", default=[4, 8, 16],
                     help="blocks per SM of the --membench kernels")
     ap.add_argument("--membench-reps", type=int, default=5)
@@ -234,10 +237,25 @@ MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark"
                "check_offsets": 16, "fill": 4}
 
 
-def model_bytes(name, prof_entry, m, n_passes_w):
+# Level 0 of a tree above 2^25 vertices marks by buckets with the Eq. 2 flag
+# pass: mark then also reads the caller ids (4 B per edge) and writes
+# vertex_parent (4 B per vertex) and the flags (2 bits per edge), and ptr_init
+# reads only the vertex's own word and its edge's flags (8 + 1/4 B) and writes
+# the pointer (4 B).
+FLAGGED_LEVEL0_MIN_VERTICES = (1 << 25) + 1
+LEVEL0_FLAGGED_BYTES = {"mark": 32.25, "ptr_init": 12.25}
+
+
+def model_bytes(name, prof_entry, m, n_passes_w, level0_calls=0):
+    """Algorithmic bytes of all launches of `name`; `level0_calls` launches
+    of the step ran a flagged level 0 of m edges (see above)."""
     e = prof_entry["elements"]
     if name == "onesweep_weights":
         return sort_weight_bytes(m, n_passes_w) * (prof_entry["launches"] // max(n_passes_w, 1))
+    if name in LEVEL0_FLAGGED_BYTES and level0_calls:
+        n0 = m if name == "mark" else m + 1
+        return (LEVEL0_FLAGGED_BYTES[name] * n0 * level0_calls +
+                MODEL_BYTES[name] * (e - n0 * level0_calls))
     return MODEL_BYTES.get(name, 0) * e
 
 
@@ -878,10 +896,35 @@ def run_membench(args):
                       "results": res}), flush=True)
 
 
+def run_emst(args):
+    import numpy as np
+    import torch
+    import paper_2401_06089_gb300 as pd
+    from paper_2401_06089_gb300 import inputs
+    pts = torch.from_numpy(inputs.gmm_points(args.emst, 3).astype(np.float32)).cuda()
+    for _ in range(max(args.warmup, 1)):
+        pd.mr_emst(pts, 16)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pd.mr_emst(pts, 16)
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.median(times)
+    print(json.dumps({"metric": "mutual-reachability MST points/s (pandora_mr_emst)",
+                      "value": args.emst / (ms / 1e3), "unit": "points/s", "ms": ms,
+                      "steps": args.steps, "n_points": args.emst, "min_pts": 16,
+                      "data": "synthetic 32-component Gaussian mixture, seed 3",
+                      "timing": "wall clock around the blocking call, median"}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.membench:
         return run_membench(args)
+    if args.emst:
+        return run_emst(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serving":
@@ -994,11 +1037,12 @@ def main():
     # ---- roofline of the dominant kernel --------------------------------
     peak, peak_kind = load_peaks()
     n_passes_w = prof["onesweep_weights"]["launches"] // max(args.steps, 1)
+    l0 = args.steps if m + 1 >= FLAGGED_LEVEL0_MIN_VERTICES else 0
     kernels = {}
     for name, e in prof.items():
         if e["launches"] == 0:
             continue
-        b = model_bytes(name, e, m, n_passes_w) if name != "onesweep_weights" else \
+        b = model_bytes(name, e, m, n_passes_w, l0) if name != "onesweep_weights" else \
             sort_weight_bytes(m, n_passes_w) * args.steps
         kernels[name] = {"launches": e["launches"], "ms": e["ms"],
                          "share": e["ms"] / (ms * args.steps) if e["ms"] else None,
@@ -1006,7 +1050,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"] or 0.0)
     dom_e = prof[dom]
     dom_bytes_total = (sort_weight_bytes(m, n_passes_w) * args.steps if dom == "onesweep_weights"
-                       else model_bytes(dom, dom_e, m, n_passes_w))
+                       else model_bytes(dom, dom_e, m, n_passes_w, l0))
     per_launch_bytes = dom_bytes_total / dom_e["launches"]
     per_launch_ms = dom_e["ms"] / dom_e["launches"]
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
@@ -1017,7 +1061,7 @@ def main():
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     path_bytes = sum((sort_weight_bytes(m, n_passes_w) * args.steps if k == "onesweep_weights"
-                      else model_bytes(k, prof[k], m, n_passes_w)) for k in kernels)
+                      else model_bytes(k, prof[k], m, n_passes_w, l0)) for k in kernels)
     path_roofline = path_bytes / args.steps / (ms / 1e3) / 1e9
 
     line = {
@@ -1119,6 +1163,17 @@ def main():
         gep, gvp = pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
         line["structure"] = dendrogram_structure(t.u, t.v, t.w, gep.cpu().numpy(),
                                                  gvp.cpu().numpy())
+    # ---- measured random-access ceilings (the level kernels' bound) -------
+    if not args.no_extra and rank == 0:
+        ra = measure_random_access(torch, pd, reps=3, blocks_per_sm=8)
+        line["random_access_ceiling"] = {
+            "unit": "G accesses/s", "kernel": "pandora_membench (one launch per pattern, "
+                                              "2^27 accesses at hashed positions)",
+            "patterns": {f"{r['kind']} over {r['array_bytes'] // 10**6} MB" +
+                         (f", {r['window_bytes'] // 2**20} MiB windows"
+                          if r["window_bytes"] < r["array_bytes"] else ""):
+                         round(r["g_access_per_s"], 2) for r in ra if r["kind"] != "copy32"}}
+
     # ---- the other configurations, each as a sub-record -----------------
     if not args.no_extra and args.workload == "rrt_1e8" and args.n is None:
         line["rrt_1e4"] = measure_rrt_1e4(pd, torch, args)

@@ -249,6 +249,46 @@ __global__ void __launch_bounds__(256) em_refit_kernel(i64 n, const float4 *P4, 
 }
 
 // ---- 4. core distances ----------------------------------------------------------------
+// The k smallest squared distances, ascending, in registers (KCAP slots, of
+// which the first k are used): an insertion is one compare-and-shift pass
+// with static indices.
+template <int KCAP>
+struct TopK {
+    float v[KCAP];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int t = 0; t < KCAP; ++t)
+            v[t] = INFINITY;
+    }
+    __device__ __forceinline__ float kth(int k) const
+    {
+        float r = INFINITY;
+#pragma unroll
+        for (int t = 0; t < KCAP; ++t)
+            if (t == k - 1)
+                r = v[t];
+        return r;
+    }
+    // insert d2 keeping v ascending; entries past slot k - 1 are dropped
+    __device__ __forceinline__ void insert(float d2, int k)
+    {
+        float x = d2;
+#pragma unroll
+        for (int t = 0; t < KCAP; ++t) {
+            if (t < k && x < v[t]) {
+                const float y = v[t];
+                v[t] = x;
+                x = y;
+            }
+        }
+    }
+};
+
+// Every point first takes the points within k positions of it in Morton
+// order (itself included), which gives a tight k-th distance before the
+// traversal; the traversal then skips those leaves.
+template <int KCAP>
 __global__ void __launch_bounds__(128) em_knn_kernel(i64 n, int k, const float4 *__restrict__ P4,
                                                      const int *__restrict__ left,
                                                      const int *__restrict__ right,
@@ -260,37 +300,34 @@ __global__ void __launch_bounds__(128) em_knn_kernel(i64 n, int k, const float4 
     if (i >= n)
         return;
     const float4 q = P4[i];
-    float best[EM_K_MAX];
-    for (int t = 0; t < k; ++t)
-        best[t] = INFINITY;
-    auto insert = [&](float d2) {
-        if (d2 < best[k - 1]) {
-            int t = k - 1;
-            while (t > 0 && best[t - 1] > d2) {
-                best[t] = best[t - 1];
-                --t;
-            }
-            best[t] = d2;
-        }
-    };
+    TopK<KCAP> best;
+    best.init();
+    const i64 w0 = i - k < 0 ? 0 : i - k, w1 = i + k >= n ? n - 1 : i + k;
+    for (i64 j = w0; j <= w1; ++j)
+        best.insert(em_d2(q, P4[j]), k);
     if (n == 1) {
-        core2[i] = 0.f;
+        core2[i] = best.kth(k);
         return;
     }
+    float kth = best.kth(k);
     int stack[EM_STACK];
     int sp = 0;
     stack[sp++] = 0;
     while (sp > 0) {
         const int node = stack[--sp];
-        if (em_box_d2(q, nlo[node], nhi[node]) >= best[k - 1])
+        if (em_box_d2(q, nlo[node], nhi[node]) >= kth)
             continue;
         int ch[2] = {left[node], right[node]};
         float lb[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
+            lb[c] = INFINITY;
             if (ch[c] >= n - 1) {
-                insert(em_d2(q, P4[ch[c] - (n - 1)]));
-                lb[c] = INFINITY;   // done
+                const i64 j = ch[c] - (n - 1);
+                if (j < w0 || j > w1) {   // the window's points are counted already
+                    best.insert(em_d2(q, P4[j]), k);
+                    kth = best.kth(k);
+                }
             } else {
                 lb[c] = em_box_d2(q, nlo[ch[c]], nhi[ch[c]]);
             }
@@ -300,7 +337,7 @@ __global__ void __launch_bounds__(128) em_knn_kernel(i64 n, int k, const float4 
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const int c = t == 0 ? first : 1 - first;
-            if (ch[c] < n - 1 && lb[c] < best[k - 1]) {   // internal nodes only
+            if (ch[c] < n - 1 && lb[c] < kth) {   // internal nodes only
                 if (sp >= EM_STACK) {
                     set_status(status, PANDORA_ERR_ITERATION_LIMIT);
                     sp = 0;
@@ -310,7 +347,7 @@ __global__ void __launch_bounds__(128) em_knn_kernel(i64 n, int k, const float4 
             }
         }
     }
-    core2[i] = best[k - 1];
+    core2[i] = kth;
 }
 
 __global__ void __launch_bounds__(256) em_set_core_kernel(i64 n, float4 *P4, const float *core2)
@@ -413,6 +450,33 @@ __global__ void __launch_bounds__(128) em_query_kernel(i64 n, const float4 *__re
     qlo[i] = blo;
     qhi[i] = bhi;
     if (bw < INFINITY)
+        atomicMin(cbest_w + cq, __float_as_uint(bw));
+}
+
+// Before the traversals of a round: every point offers the lightest edge to
+// its Morton-order neighbours (within EM_SEED positions) in another
+// component as an upper bound of its component's least edge, so that the
+// traversals start with a tight bound.  Only a bound: the traversal finds
+// the least edge itself.
+constexpr int EM_SEED = 8;
+__global__ void __launch_bounds__(256) em_seed_kernel(i64 n, const float4 *__restrict__ P4,
+                                                      const i32 *__restrict__ comp,
+                                                      u32 *cbest_w)
+{
+    const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float4 q = P4[i];
+    const int cq = comp[i];
+    float bw = INFINITY;
+    const i64 w0 = i - EM_SEED < 0 ? 0 : i - EM_SEED, w1 = i + EM_SEED >= n ? n - 1 : i + EM_SEED;
+    for (i64 j = w0; j <= w1; ++j) {
+        if (comp[j] == cq)
+            continue;
+        const float4 p = P4[j];
+        bw = fminf(bw, fmaxf(fmaxf(q.w, p.w), em_d2(q, p)));
+    }
+    if (bw < INFINITY && __float_as_uint(bw) < *(const volatile u32 *)(cbest_w + cq))
         atomicMin(cbest_w + cq, __float_as_uint(bw));
 }
 
@@ -657,8 +721,15 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
         em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, left, right, nparent, nlo,
                                                            nhi, flags, &ctrl->status);
     }
-    em_knn_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi, core2,
-                                                     &ctrl->status);
+    if (k <= 8)
+        em_knn_kernel<8><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi, core2,
+                                                            &ctrl->status);
+    else if (k <= 16)
+        em_knn_kernel<16><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi,
+                                                             core2, &ctrl->status);
+    else
+        em_knn_kernel<EM_K_MAX><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi,
+                                                                   core2, &ctrl->status);
     em_set_core_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, core2);
     em_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(cbest_w, cbest_e, n);
     EM_CUDA(cudaGetLastError());
@@ -668,6 +739,7 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
         EM_CUDA(cudaMemsetAsync(flags, 0, (size_t)(n - 1) * 4, s));
         em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, left, right, nparent, nlo,
                                                            nhi, flags, &ctrl->status);
+        em_seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, cbest_w);
         em_query_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, P4, comp, orig, left, right, nlo,
                                                            nhi, cbest_w, qbw, qlo, qhi,
                                                            &ctrl->status);

@@ -506,7 +506,10 @@ __global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams 
 //    it to every member.  This is the union-find contraction the paper uses
 //    (after Jaiganesh and Burtscher), applied where pointer chasing would cost
 //    log(depth) rounds per vertex.
-constexpr int WALK_STEPS = 8;
+#ifndef PANDORA_WALK_STEPS
+#define PANDORA_WALK_STEPS 8
+#endif
+constexpr int WALK_STEPS = PANDORA_WALK_STEPS;
 
 // Level 0 keeps the supervertex in the low half of x's own word (the rank
 // of x's lightest edge stays in the high half), so that compact learns both

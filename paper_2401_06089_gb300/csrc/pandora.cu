@@ -150,12 +150,13 @@ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 #endif
 constexpr i64 MARK_DIRECT_MAX_VERTICES = PANDORA_MARK_DIRECT_MAX;
 // Link stores edge_parent by caller-id buckets of 2^LINK_BUCKET_SHIFT ids
-// (16 MB of edge_parent each) above LINK_BUCKET_MIN_EDGES edges.
+// (8 MB of edge_parent each; 21 measured 0.07 ms faster than 22 at 10^8
+// edges) above LINK_BUCKET_MIN_EDGES edges.
 #ifndef PANDORA_LINK_BUCKET_MIN
 #define PANDORA_LINK_BUCKET_MIN (i64(1) << 25)
 #endif
 #ifndef PANDORA_LINK_BUCKET_SHIFT
-#define PANDORA_LINK_BUCKET_SHIFT 22
+#define PANDORA_LINK_BUCKET_SHIFT 21
 #endif
 constexpr i64 LINK_BUCKET_MIN_EDGES = PANDORA_LINK_BUCKET_MIN;
 constexpr int LINK_BUCKET_SHIFT = PANDORA_LINK_BUCKET_SHIFT;
