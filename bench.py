@@ -1142,6 +1142,13 @@ def main():
     # ---- HDBSCAN* flat clusters on the same dendrogram (optional) ----------
     if args.flat and rank == 0:
         pd.dendrogram(u, v, w, workspace=ws, out=(ep, vp))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        labels = pd.hdbscan_labels(ep, vp, w, args.flat)
+        torch.cuda.synchronize()
+        # the library's pool keeps what the call took: the drop in free memory
+        # is the call's scratch high-water mark (outputs come from torch)
+        flat_scratch = free0 - torch.cuda.mem_get_info()[0] - labels.numel() * 4
         for _ in range(max(args.warmup, 3)):
             labels = pd.hdbscan_labels(ep, vp, w, args.flat)
         torch.cuda.synchronize()
@@ -1156,6 +1163,7 @@ def main():
         ms3 = a.elapsed_time(b) / k3
         lab_np = labels.cpu().numpy()
         line["flat_clusters"] = {"min_cluster_size": args.flat, "ms_per_call": ms3,
+                                 "scratch_bytes": int(flat_scratch),
                                  "points_per_s": (m + 1) / (ms3 / 1e3), "steps": k3,
                                  "clusters": int(lab_np.max()) + 1,
                                  "noise_fraction": float((lab_np < 0).mean())}

@@ -107,9 +107,17 @@ __device__ __forceinline__ i32 after_arc(i32 c, i32 m, const i32 *par, const i32
 
 // ---- 1. parents and validation --------------------------------------------
 // Children of edge p: the smaller node id in kids[2p], the larger in
-// kids[2p + 1] (any fixed order serves the tour).
+// kids[2p + 1] (any fixed order serves the tour).  Each child makes two
+// updates at its parent: an atomicMin of its id into kids[2p], and one 64-bit
+// add of 2^32 + id into cnt[p], which counts the children in the high half and
+// sums their ids in the low half; flat_check recovers the larger child as the
+// sum minus the smaller once it has checked the count is two.  Node ids are
+// below 2^30, so two of them never carry out of the low half, and carries of
+// three or more only raise the count: a high half of exactly 2 means exactly
+// two children.
+constexpr int CNT_SHIFT = 32;
 __global__ void flat_parents_kernel(const i32 *ep, const i32 *vp, const float *w, i32 m, i32 n,
-                                    i32 *par, i32 *cnt, i32 *kids, FlatCtrl *c)
+                                    i32 *par, u64 *cnt, i32 *kids, FlatCtrl *c)
 {
     const i64 N = (i64)m + n;
     for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < N;
@@ -135,15 +143,14 @@ __global__ void flat_parents_kernel(const i32 *ep, const i32 *vp, const float *w
             continue;
         }
         par[i] = p;
-        // no return values: the three updates issue as reductions
-        atomicAdd(&cnt[p], 1);
+        // no return values: the two updates issue as reductions
+        atomicAdd((unsigned long long *)&cnt[p], (1ull << CNT_SHIFT) + (u64)i);
         atomicMin(&kids[2 * (i64)p], (i32)i);
-        atomicMax(&kids[2 * (i64)p + 1], (i32)i);
     }
 }
 
-// kids[2e] = INT32_MAX and kids[2e + 1] = -1 (for the min / max above), cnt = 0.
-__global__ void kids_init_kernel(i32 m, i32 *kids, i32 *cnt)
+// kids[2e] = INT32_MAX and kids[2e + 1] = -1 (for the minimum above), cnt = 0.
+__global__ void kids_init_kernel(i32 m, i32 *kids, u64 *cnt)
 {
     for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
          e += (i64)gridDim.x * blockDim.x) {
@@ -153,15 +160,22 @@ __global__ void kids_init_kernel(i32 m, i32 *kids, i32 *cnt)
 }
 
 // Two children per edge, one root, and every parent after its child in the
-// (weight, index) order (which also rules out cycles).
-__global__ void flat_check_kernel(const float *w, i32 m, const i32 *par, const i32 *cnt,
-                                  FlatCtrl *c)
+// (weight, index) order (which also rules out cycles); the larger child from
+// the children's id sum.
+__global__ void flat_check_kernel(const float *w, i32 m, const i32 *par, const u64 *cnt,
+                                  i32 *kids, FlatCtrl *c)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && c->n_roots != 1)
         set_status(&c->status, PANDORA_ERR_NOT_A_DENDROGRAM);
     for (i64 e = blockIdx.x * (i64)blockDim.x + threadIdx.x; e < m;
          e += (i64)gridDim.x * blockDim.x) {
-        bool ok = cnt[e] == 2;
+        const u64 ce = cnt[e];
+        bool ok = (ce >> CNT_SHIFT) == 2u;
+        if (ok) {
+            const i64 other = (i64)(u32)ce - kids[2 * e];
+            ok = other > kids[2 * e] && other < (i64)m + m + 1;
+            kids[2 * e + 1] = ok ? (i32)other : -1;
+        }
         const i32 p = par[e];
         if (p >= 0) {
             const float wp = w[p], we = w[e];
@@ -1302,7 +1316,8 @@ struct Carve {
 
 struct FlatLayout {
     FlatCtrl *ctrl;
-    i32 *par, *cnt, *kids, *size, *head, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
+    i32 *par, *kids, *size, *head, *start, *cid, *bsum, *lcl, *lab, *flag, *rank;
+    u64 *cnt;               // children of every edge: count << 40 | sum of their ids
     u64 *arcA, *arcB;       // tour words, then suffix sums (A); (segment, offset) (B)
     i32 *sid_of, *spl;      // ruling set: splitter id per arc, splitter arcs
     u64 *segA, *segB;       // ruling set: segment words
@@ -1325,7 +1340,7 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     FlatLayout l;
     l.ctrl = cv.take<FlatCtrl>(1);
     l.par = cv.take<i32>(N);
-    l.cnt = cv.take<i32>(m);
+    l.cnt = cv.take<u64>(m);
     l.kids = cv.take<i32>(2 * m);
     l.size = cv.take<i32>(m);
     l.head = cv.take<i32>(m);
@@ -1353,6 +1368,16 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     l.hdB = cv.take<i32>(l.bp_cap);
     l.rec = cv.take<u64>(n);
     l.bagg = cv.take<u64>(nb);
+    l.bytes = cv.off + 256;
+    return l;
+}
+
+// The per-cluster arrays (about 600 bytes per cluster, most of it the tree
+// contraction's 448-bit edge functions), carved from a second block once the
+// cluster count K is known.
+size_t cluster_layout(FlatLayout &l, char *base, i64 Kmax)
+{
+    Carve cv{base};
     l.first = cv.take<i32>(Kmax);
     l.cpar = cv.take<i32>(Kmax);
     l.ckids = cv.take<i32>(2 * Kmax);
@@ -1382,8 +1407,7 @@ FlatLayout flat_layout(char *base, i64 n, i64 Kmax)
     E.rk_k = cv.take<Big>(Kmax);
     E.rk_as = cv.take<Big>(Kmax);
     E.rk_bs = cv.take<Big>(Kmax);
-    l.bytes = cv.off + 256;
-    return l;
+    return cv.off + 256;
 }
 
 // Grid of a grid-stride kernel: one block per FT items, at most 8 blocks per
@@ -1427,9 +1451,9 @@ void fill_records(u64 *data, i64 len, u64 *bagg, cudaStream_t s)
     fill_down_kernel<<<(unsigned)nb, FT, 0, s>>>(data, len, bagg);
 }
 
-int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *w, i64 n,
-                i32 mcs, i64 Kmax, i32 *labels, double *stab_out, i64 *n_clusters,
-                cudaStream_t s)
+int run_flat_on(FlatLayout &l, const i32 *ep, const i32 *vp, const float *w, i64 n, i32 mcs,
+                i64 Kmax, i32 *labels, double *stab_out, i64 *n_clusters, cudaMemPool_t pool,
+                void **cluster_ws, cudaStream_t s)
 {
     const i64 m = n - 1, N = m + n, L = 2 * m + n;
     FlatCtrl *c = l.ctrl;
@@ -1439,7 +1463,7 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
 
     // 1. parents and validation
     flat_parents_kernel<<<grid_for(N), FT, 0, s>>>(ep, vp, w, mi, ni, l.par, l.cnt, l.kids, c);
-    flat_check_kernel<<<grid_for(m), FT, 0, s>>>(w, mi, l.par, l.cnt, c);
+    flat_check_kernel<<<grid_for(m), FT, 0, s>>>(w, mi, l.par, l.cnt, l.kids, c);
     if (n >= mcs) {
         // 2. leaf counts
         tour_init_kernel<<<grid_for(L), FT, 0, s>>>(mi, ni, l.par, l.kids, l.arcA, c);
@@ -1504,6 +1528,25 @@ int run_flat_on(const FlatLayout &l, const i32 *ep, const i32 *vp, const float *
         anchor_mark_kernel<<<grid_for(N), FT, 0, s>>>(mi, ni, mcs, l.par, l.size, l.head, l.cid,
                                                       suf, l.rec, c);
         fill_records(l.rec, n, l.bagg, s);
+        {
+            // the cluster count is known now: size the per-cluster arrays by it
+            FlatCtrl h{};
+            if (cudaMemcpyAsync(&h, c, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PANDORA_ERR_CUDA;
+            if (h.status)
+                return h.status;
+            if (h.n_starts < 1 || (i64)h.n_starts > Kmax)
+                return PANDORA_ERR_NOT_A_DENDROGRAM;   // more clusters than n / mcs allows
+            Kmax = h.n_starts;
+            const size_t cbytes = cluster_layout(l, nullptr, Kmax);
+            if (cudaMallocFromPoolAsync(cluster_ws, cbytes, pool, s) != cudaSuccess) {
+                cudaGetLastError();
+                *cluster_ws = nullptr;
+                return PANDORA_ERR_OUT_OF_MEMORY;
+            }
+            cluster_layout(l, (char *)(((uintptr_t)*cluster_ws + 255) & ~(uintptr_t)255), Kmax);
+        }
         cudaMemsetAsync(l.ccnt, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.sel, 0, sizeof(i32) * Kmax, s);
         cudaMemsetAsync(l.acc, 0, sizeof(u64) * Kmax * NL, s);
@@ -1590,13 +1633,16 @@ int run_flat(const i32 *ep, const i32 *vp, const float *w, i64 n, i32 mcs, i32 *
     cudaMemPool_t pool = flat_pool(dev);
     if (!pool)
         return PANDORA_ERR_CUDA;
-    void *ws = nullptr;
+    void *ws = nullptr, *cws = nullptr;
     if (cudaMallocFromPoolAsync(&ws, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return PANDORA_ERR_OUT_OF_MEMORY;
     }
-    const int st = run_flat_on(flat_layout((char *)ws, n, Kmax), ep, vp, w, n, mcs, Kmax,
-                               labels, stab_out, n_clusters, s);
+    FlatLayout l = flat_layout((char *)ws, n, Kmax);
+    const int st = run_flat_on(l, ep, vp, w, n, mcs, Kmax, labels, stab_out, n_clusters, pool,
+                               &cws, s);
+    if (cws)
+        cudaFreeAsync(cws, s);
     cudaFreeAsync(ws, s);
     if (st != PANDORA_OK)
         cudaStreamSynchronize(s);
