@@ -288,8 +288,11 @@ struct TopK {
 // Every point first takes the points within k positions of it in Morton
 // order (itself included), which gives a tight k-th distance before the
 // traversal; the traversal then skips those leaves.
+#ifndef PANDORA_EM_KNN_MINB
+#define PANDORA_EM_KNN_MINB 1
+#endif
 template <int KCAP>
-__global__ void __launch_bounds__(128) em_knn_kernel(i64 n, int k, const float4 *__restrict__ P4,
+__global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n, int k, const float4 *__restrict__ P4,
                                                      const int *__restrict__ left,
                                                      const int *__restrict__ right,
                                                      const float4 *__restrict__ nlo,
@@ -368,7 +371,10 @@ __device__ __forceinline__ float em_comp_bound(const u32 *cbest_w, int c)
     return __uint_as_float(*(const volatile u32 *)(cbest_w + c));
 }
 
-__global__ void __launch_bounds__(128) em_query_kernel(i64 n, const float4 *__restrict__ P4,
+#ifndef PANDORA_EM_QUERY_MINB
+#define PANDORA_EM_QUERY_MINB 1
+#endif
+__global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i64 n, const float4 *__restrict__ P4,
                                                        const i32 *__restrict__ comp,
                                                        const u32 *__restrict__ orig,
                                                        const int *__restrict__ left,
