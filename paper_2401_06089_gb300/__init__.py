@@ -25,6 +25,7 @@ from ._binding import (  # noqa: F401
     mr_emst,
     set_tuning,
     set_wait_report_limit,
+    sort_pairs,
     status_string,
     workspace_size,
     workspace_status,

@@ -110,6 +110,8 @@ def load_library():
                                          ctypes.c_int, P]
         lib.pandora_mr_emst.argtypes = [P, I64, ctypes.c_int32, P, P, P, P, P]
         lib.pandora_set_wait_report_limit.argtypes = [I64]
+        lib.pandora_sort_pairs_workspace_size.argtypes = [I64, ctypes.c_int32, ctypes.POINTER(SZ)]
+        lib.pandora_sort_pairs.argtypes = [P, P, I64, ctypes.c_int32, P, P, P, SZ, P]
         for name in ("pandora_dendrogram", "pandora_dendrogram_ws", "pandora_dendrogram_batched",
                      "pandora_dendrogram_batched_ws", "pandora_workspace_size",
                      "pandora_version", "pandora_profile_start", "pandora_profile_read",
@@ -117,7 +119,8 @@ def load_library():
                      "pandora_workspace_status", "pandora_set_tuning", "pandora_get_tuning",
                      "pandora_dendrogram_batched_planned", "pandora_dendrogram_host",
                      "pandora_hdbscan_labels", "pandora_membench", "pandora_mr_emst",
-                     "pandora_set_wait_report_limit"):
+                     "pandora_set_wait_report_limit", "pandora_sort_pairs_workspace_size",
+                     "pandora_sort_pairs"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     _apply_default_tuning()
@@ -548,6 +551,38 @@ def mr_emst(points, min_pts: int, *, core: bool = False):
     if st:
         raise PandoraError(st, "pandora_mr_emst")
     return (u, v, w, cs) if core else (u, v, w)
+
+
+def sort_pairs(keys, vals, key_bits: int = 32):
+    """Stable radix sort of (key, value) pairs by key (``pandora_sort_pairs``,
+    the sort of the dendrogram's weight and chain-key steps): keys and vals
+    are contiguous 4-byte CUDA tensors of equal length, every key below
+    2^key_bits; returns new (keys, vals) tensors in key order, equal keys in
+    input order.  Synchronises the current stream."""
+    torch = _torch()
+    for name, t in (("keys", keys), ("vals", vals)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+                and t.element_size() == 4):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of 4-byte elements")
+    if keys.numel() != vals.numel():
+        raise ValueError("keys and vals differ in length")
+    n = keys.numel()
+    dev = keys.device
+    lib = load_library()
+    need = ctypes.c_size_t()
+    st = lib.pandora_sort_pairs_workspace_size(n, int(key_bits), ctypes.byref(need))
+    if st:
+        raise PandoraError(st, "pandora_sort_pairs_workspace_size")
+    ws = torch.empty(max(need.value, 16), dtype=torch.uint8, device=dev)
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    with torch.cuda.device(dev):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        st = lib.pandora_sort_pairs(_ptr(keys), _ptr(vals), n, int(key_bits), _ptr(ko), _ptr(vo),
+                                    _ptr(ws), ws.numel(), stream)
+    if st:
+        raise PandoraError(st, "pandora_sort_pairs")
+    return ko, vo
 
 
 def set_wait_report_limit(spins: int) -> None:

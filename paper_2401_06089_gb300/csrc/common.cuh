@@ -33,9 +33,9 @@ struct Ctrl {
     u64 n_deep;                    // vertices left to union-find by the bounded walk
     u32 tile_counter[16];          // dynamic tile ids of single-pass kernels
     u32 hist1[4][256];             // digit histograms of the (weight, index) sort
-    u32 hist2[4][256];             // digit histograms of the chain-key sort
     u32 base1[4][256];             // their exclusive scans (bucket starts)
-    u32 base2[4][256];
+    u32 hist2[4096];               // digit histograms of the chain-key sort, rows of its digit plan
+    u32 base2[4096];               // their exclusive scans
     // bucketed marking (levels with many vertices): incidences per vertex
     // bucket, write cursors, bucket starts
     u32 mark_count[MARK_MAX_BUCKETS];

@@ -59,7 +59,25 @@ struct OnesweepParams {
     const i64 *edge_off;   // OS_FOREST
     i64 n_trees;
     u32 report_limit = SPIN_LIMIT;   // look-back waits longer than this record ITERATION_LIMIT
+    int dbits = 8;         // digit width (9 only for the key-value sort, OS_WRITE_KEYS)
 };
+
+// Digit plan of an LSD sort: pass q sorts by the `width[q]` bits above
+// `shift[q]`; its histogram row (2^width[q] counts) starts at off[q].
+struct DigitPlan {
+    int n;
+    int shift[4];
+    int width[4];
+    int off[4];
+};
+// Plan for keys of `bits` significant bits: three passes of 8 or 9 bits for
+// 25 to 27 bits, else 8-bit digits.  (Three passes over 28 to 30 bits need a
+// 10-bit digit, whose 4096-key tiles write runs of four keys per digit: at
+// 10^8 chain keys 10 + 9 + 9 bits took 3.54 ms against 2.94 ms for four
+// 8-bit passes, while 9 + 9 + 8 bits at 2 * 10^7 took 0.60 against 0.64.)
+DigitPlan digit_plan(int bits);
+constexpr int DIGIT_PLAN_HIST = 4096;   // histogram entries of the widest plan
+static_assert(sizeof(((Ctrl *)nullptr)->hist2) == DIGIT_PLAN_HIST * 4, "chain histogram size");
 
 __host__ __device__ inline i64 onesweep_tiles(i64 n) { return (n + OS_TILE - 1) / OS_TILE; }
 
@@ -70,9 +88,11 @@ void launch_onesweep(int flags, const OnesweepParams &p, cudaStream_t s);
 void launch_hist_keys(const u32 *keys, i64 n, u32 *hist, cudaStream_t s);
 // base[r][d] = sum of hist[r][d'] over d' < d, for `rows` rows of 256
 void launch_hist_scan(const u32 *hist, u32 *base, int rows, cudaStream_t s);
+// base = exclusive scan of every row of a digit plan's histogram
+void launch_hist_scan_plan(const u32 *hist, u32 *base, const DigitPlan &plan, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// levels.cu - one contraction level (Eq. 1, Eq. 2, Section 3.2)
+// levels.cu, mark.cu - one contraction level (Eq. 1, Eq. 2, Section 3.2)
 // ---------------------------------------------------------------------------
 constexpr int LV_THREADS = 256;
 constexpr int LV_ITEMS = 8;
@@ -161,6 +181,36 @@ u32 wait_report_limit();
 
 __host__ __device__ inline i64 eflag_words(i64 m) { return (m + 15) / 16; }
 
+// Level kernels run only while the loop is open: once a level without
+// alpha-edges has set n_levels, kernels launched for later (bound) levels
+// exit at once.
+__device__ __forceinline__ bool loop_closed(const LevelParams &p)
+{
+    return *(const volatile int *)p.d_n_levels != 0;
+}
+
+// Blocks for n elements at per_block each, capped at PANDORA_LV_BPS blocks
+// per SM: every level kernel loops (grid-stride or over claimed tiles), so a
+// grid sized for a worst-case bound does not launch idle blocks by the
+// million.  The level kernels are bound by random DRAM reads: 8 blocks per SM
+// measured 0.2 ms faster than 4 over all levels of a 10^8-edge random
+// recursive tree, while the union-find part ran 20% faster at 4 blocks per SM
+// than at 16 on a 10^8-vertex path (PANDORA_UF_BPS).
+#ifndef PANDORA_LV_BPS
+#define PANDORA_LV_BPS 8
+#endif
+#ifndef PANDORA_UF_BPS
+#define PANDORA_UF_BPS 4
+#endif
+inline unsigned grid_for(i64 n, int per_block, int bps = PANDORA_LV_BPS)
+{
+    i64 b = (n + per_block - 1) / per_block;
+    const i64 cap = 152 * bps;
+    if (b > cap)
+        b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
 void launch_init_level(const LevelParams &p, cudaStream_t s);   // min_word = NO_EDGE
 void launch_mark(const LevelParams &p, cudaStream_t s);   // with eflag: also the flag pass
 void launch_ptr_init(const LevelParams &p, cudaStream_t s);
@@ -168,7 +218,7 @@ void launch_compress(const LevelParams &p, cudaStream_t s);   // walk + union-fi
 void launch_compact(const LevelParams &p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// expand.cu - multilevel expansion (Section 3.3.2) and chain linking (3.3.3)
+// expand.cu, link.cu - multilevel expansion (Section 3.3.2) and chain linking (3.3.3)
 // ---------------------------------------------------------------------------
 struct LevelTable {
     const int2 *rec[MAX_LEVELS];   // {chain key, supervertex} of every vertex of level l >= 1
@@ -187,7 +237,8 @@ struct ExpandParams {
     u32 root_base;
     const i64 *edge_off;   // forest mode
     i64 n_trees;
-    u32 *hist;             // [4][256] digit histograms of the chain keys
+    u32 *hist;             // digit histograms of the chain keys, rows of `plan`
+    DigitPlan plan;
     int *status;
 };
 

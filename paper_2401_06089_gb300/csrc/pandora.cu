@@ -162,6 +162,23 @@ constexpr i64 LINK_BUCKET_MIN_EDGES = PANDORA_LINK_BUCKET_MIN;
 constexpr int LINK_BUCKET_SHIFT = PANDORA_LINK_BUCKET_SHIFT;
 constexpr int MARK_BUCKET_SHIFT = PANDORA_MARK_BUCKET_SHIFT;
 
+// Digit plan of the chain-key sort: keys are 2 * rank + side below 2M and
+// root keys 2M .. 2M + T - 1, so the plan follows the bits of 2M + T - 1.
+// PANDORA_CHAIN_WIDE_DIGITS=0 keeps 8-bit digits at every key width.
+#ifndef PANDORA_CHAIN_WIDE_DIGITS
+#define PANDORA_CHAIN_WIDE_DIGITS 1
+#endif
+DigitPlan chain_digit_plan(i64 M, i64 T)
+{
+    const u64 max_key = (u64)(2 * M) + (u64)T - 1;
+    int bits = 0;
+    while (bits < 32 && (max_key >> bits) != 0)
+        ++bits;
+    if (!PANDORA_CHAIN_WIDE_DIGITS && bits > 24 && bits <= 27)
+        bits = 31;   // four 8-bit passes
+    return digit_plan(bits);
+}
+
 struct Layout {
     size_t ctrl, keysA, keysB, valsA, valsB, perm, ab0, lb, min_word, ptr;
     size_t deep, uf, root_of;
@@ -186,7 +203,12 @@ Layout make_layout(i64 M, i64 T)
     L.valsB = take(M * 4);
     L.perm = take(M * 4);
     L.ab0 = take(M * 8);
-    const i64 os_words = onesweep_tiles(M) * RADIX;
+    // look-back words of the widest pass (the chain sort may use 9- or 10-bit digits)
+    const DigitPlan cpl = chain_digit_plan(M, T);
+    int widest = 8;
+    for (int q = 0; q < cpl.n; ++q)
+        widest = std::max(widest, cpl.width[q]);
+    const i64 os_words = onesweep_tiles(M) * ((i64)1 << widest);
     const i64 lv_words = level_tiles(N) + 1 + level_tiles(M) + 1;
     L.lb_words = std::max(os_words, lv_words);
     L.lb = take(L.lb_words * 8);
@@ -623,28 +645,35 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     E.root_base = root_base;
     E.edge_off = d_off;
     E.n_trees = T;
-    E.hist = &ctrl->hist2[0][0];
+    E.hist = ctrl->hist2;
+    E.plan = chain_digit_plan(M, T);
     E.status = status;
+    const DigitPlan &plan = E.plan;
     timer.launch(K_EXPAND, M, 2, [&] {
         launch_expand(E, table, s);
-        launch_hist_scan(&ctrl->hist2[0][0], &ctrl->base2[0][0], 4, s);
+        launch_hist_scan_plan(ctrl->hist2, ctrl->base2, plan, s);
     });
     PANDORA_CUDA(cudaGetLastError());
-    const u64 max_key = (u64)root_base + (u64)T - 1;
-    int bits = 0;
-    while (bits < 32 && (max_key >> bits) != 0)
-        ++bits;
     std::vector<int> passes2;
-    for (int q = 0; q < (bits + 7) / 8; ++q)
+    for (int q = 0; q < plan.n; ++q)
         passes2.push_back(q);
     if (blocking) {
-        static thread_local u32 hhist2[4][RADIX];
+        static thread_local u32 hhist2[DIGIT_PLAN_HIST];
         PANDORA_CUDA(cudaMemcpyAsync(hhist2, ctrl->hist2, sizeof(hhist2), cudaMemcpyDeviceToHost, s));
         if (int e = read_counters(ctrl, &h, s))
             return e;
         if (h.status)
             return h.status;
-        passes2 = useful_passes(hhist2, (bits + 7) / 8, M);
+        // a pass whose digit is the same for every key is the identity
+        passes2.clear();
+        for (int q = 0; q < plan.n; ++q) {
+            bool trivial = false;
+            for (int d = 0; d < (1 << plan.width[q]); ++d)
+                if ((i64)hhist2[plan.off[q] + d] == M)
+                    trivial = true;
+            if (!trivial)
+                passes2.push_back(q);
+        }
     }
 
     // ---- 4. stable sort by chain key, then link -------------------------------
@@ -653,9 +682,11 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         OnesweepParams P{};
         P.report_limit = report;
         P.n = M;
-        P.shift = 8 * passes2[k];
-        P.hist = ctrl->hist2[passes2[k]];
-        P.bin_base = ctrl->base2[passes2[k]];
+        const int q = passes2[k];
+        P.shift = plan.shift[q];
+        P.dbits = plan.width[q];
+        P.hist = ctrl->hist2 + plan.off[q];
+        P.bin_base = ctrl->base2 + plan.off[q];
         P.lb = lb;
         P.tile_counter = &ctrl->tile_counter[0];
         P.status = status;
@@ -664,7 +695,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         const bool outB = (sk == keysA);
         P.keys_out = outB ? keysB : keysA;
         P.vals_out = outB ? valsB : valsA;
-        PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
+        PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * (1 << P.dbits) * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
         timer.launch(K_SORT_CHAINS, M, [&] { launch_onesweep(OS_WRITE_KEYS, P, s); });
         sk = P.keys_out;
