@@ -237,21 +237,36 @@ MODEL_BYTES = {"hist_weights": 4, "onesweep_chains": 16, "init_level": 8, "mark"
                "check_offsets": 16, "fill": 4}
 
 
-# Level 0 of a tree above 2^25 vertices marks by buckets with the Eq. 2 flag
+# Level 0 of a tree above 2^24 vertices marks by buckets with the Eq. 2 flag
 # pass: mark then also reads the caller ids (4 B per edge) and writes
-# vertex_parent (4 B per vertex) and the flags (2 bits per edge), and ptr_init
+# vertex_parent (4 B per vertex) and the flags (2 bits per edge); ptr_init
 # reads only the vertex's own word and its edge's flags (8 + 1/4 B) and writes
-# the pointer (4 B).
-FLAGGED_LEVEL0_MIN_VERTICES = (1 << 25) + 1
-LEVEL0_FLAGGED_BYTES = {"mark": 32.25, "ptr_init": 12.25}
+# the pointer (4 B); root finding reads and tags the pointer words (own word
+# read and written, at least one pointer target read: 12 B); compact (see
+# compact_level0_bytes) reads the pointer tag of one endpoint of a contracted
+# edge and of both endpoints of an alpha-edge.
+FLAGGED_LEVEL0_MIN_VERTICES = (1 << 24) + 1
+LEVEL0_FLAGGED_BYTES = {"mark": 32.25, "ptr_init": 12.25, "compress": 12}
 
 
-def model_bytes(name, prof_entry, m, n_passes_w, level0_calls=0):
+def compact_level0_bytes(m, m1):
+    """Flagged level-0 compact of m edges of which m1 are alpha-edges: every
+    edge reads its endpoints and flags (8 + 1/4 B); a contracted edge reads one
+    4-byte tag and writes its level and supervertex (1 + 4 B); an alpha-edge
+    reads two tags and writes its relabelled endpoints and rank (8 + 4 B)."""
+    return m * 8.25 + (m - m1) * 9 + m1 * 20
+
+
+def model_bytes(name, prof_entry, m, n_passes_w, level0_calls=0, m1=0):
     """Algorithmic bytes of all launches of `name`; `level0_calls` launches
-    of the step ran a flagged level 0 of m edges (see above)."""
+    of the step ran a flagged level 0 of m edges with m1 alpha-edges (see
+    above)."""
     e = prof_entry["elements"]
     if name == "onesweep_weights":
         return sort_weight_bytes(m, n_passes_w) * (prof_entry["launches"] // max(n_passes_w, 1))
+    if name == "compact" and level0_calls:
+        return (compact_level0_bytes(m, m1) * level0_calls +
+                MODEL_BYTES[name] * (e - m * level0_calls))
     if name in LEVEL0_FLAGGED_BYTES and level0_calls:
         n0 = m if name == "mark" else m + 1
         return (LEVEL0_FLAGGED_BYTES[name] * n0 * level0_calls +
@@ -1038,11 +1053,12 @@ def main():
     peak, peak_kind = load_peaks()
     n_passes_w = prof["onesweep_weights"]["launches"] // max(args.steps, 1)
     l0 = args.steps if m + 1 >= FLAGGED_LEVEL0_MIN_VERTICES else 0
+    m1 = stats["level_edges"][1] if len(stats["level_edges"]) > 1 else 0
     kernels = {}
     for name, e in prof.items():
         if e["launches"] == 0:
             continue
-        b = model_bytes(name, e, m, n_passes_w, l0) if name != "onesweep_weights" else \
+        b = model_bytes(name, e, m, n_passes_w, l0, m1) if name != "onesweep_weights" else \
             sort_weight_bytes(m, n_passes_w) * args.steps
         kernels[name] = {"launches": e["launches"], "ms": e["ms"],
                          "share": e["ms"] / (ms * args.steps) if e["ms"] else None,
@@ -1050,7 +1066,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"] or 0.0)
     dom_e = prof[dom]
     dom_bytes_total = (sort_weight_bytes(m, n_passes_w) * args.steps if dom == "onesweep_weights"
-                       else model_bytes(dom, dom_e, m, n_passes_w, l0))
+                       else model_bytes(dom, dom_e, m, n_passes_w, l0, m1))
     per_launch_bytes = dom_bytes_total / dom_e["launches"]
     per_launch_ms = dom_e["ms"] / dom_e["launches"]
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
@@ -1061,7 +1077,7 @@ def main():
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     path_bytes = sum((sort_weight_bytes(m, n_passes_w) * args.steps if k == "onesweep_weights"
-                      else model_bytes(k, prof[k], m, n_passes_w, l0)) for k in kernels)
+                      else model_bytes(k, prof[k], m, n_passes_w, l0, m1)) for k in kernels)
     path_roofline = path_bytes / args.steps / (ms / 1e3) / 1e9
 
     line = {

@@ -149,6 +149,15 @@ inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 #define PANDORA_MARK_BUCKET_SHIFT 21
 #endif
 constexpr i64 MARK_DIRECT_MAX_VERTICES = PANDORA_MARK_DIRECT_MAX;
+// Level 0 goes bucketed from a lower size: there the bucketed form also runs
+// the flag pass, which removes two random reads per vertex from ptr_init and
+// one per contracted edge from compact.  Random recursive trees, ms per
+// dendrogram, direct / bucketed level 0: 3.2*10^7 edges 8.86 / 8.26,
+// 2.4*10^7 6.33 / 6.15, 1.2*10^7 3.32 / 3.47, 6*10^6 2.10 / 2.26.
+#ifndef PANDORA_MARK_DIRECT_MAX0
+#define PANDORA_MARK_DIRECT_MAX0 (i64(1) << 24)
+#endif
+constexpr i64 MARK_DIRECT_MAX0_VERTICES = PANDORA_MARK_DIRECT_MAX0;
 // Link stores edge_parent by caller-id buckets of 2^LINK_BUCKET_SHIFT ids
 // (8 MB of edge_parent each; 21 measured 0.07 ms faster than 22 at 10^8
 // edges) above LINK_BUCKET_MIN_EDGES edges.
@@ -550,7 +559,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         // above L2; its records live in arrays idle during the level loop:
         // the sort buffers (keysA .. valsB, 16 M bytes) and, on level 0, the
         // kept records (filled from level 1 on)
-        if (n_grid > MARK_DIRECT_MAX_VERTICES) {
+        if (n_grid > (l == 0 ? MARK_DIRECT_MAX0_VERTICES : MARK_DIRECT_MAX_VERTICES)) {
             // buckets of 2^MARK_BUCKET_SHIFT vertices, wider when the level
             // would need more than MARK_MAX_BUCKETS of them
             int shift = MARK_BUCKET_SHIFT;

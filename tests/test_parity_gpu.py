@@ -252,6 +252,16 @@ def test_hdbscan_shaped_tree(pd):
     pins.check_invariants(t.u, t.v, t.w, ep, vp)
 
 
+@pytest.mark.parametrize("family", ["rrt", "path_skewed"])
+def test_between_level0_and_level1_bucketing_thresholds(pd, family):
+    """2*10^7 vertices: level 0 (above 2^24 vertices) marks by buckets with the
+    flag pass while level 1 marks directly, and the chain keys (26 bits) take
+    the three-pass 9 + 9 + 8-bit sort; every element against the oracle."""
+    n = 20_000_000
+    t = inputs.rrt(n, 5) if family == "rrt" else inputs.path_skewed(n, 6)
+    assert_parity(pd, t)
+
+
 # ---- full size, in the launch configuration bench.py times ---------------------
 
 @pytest.mark.parametrize("family", ["rrt", "path_skewed"])
@@ -275,7 +285,7 @@ def test_full_size_1e8(pd, family):
 
 def test_batched_forest_above_bucketed_marking_threshold(pd):
     """A forest of 4.4*10^7 vertices: level 0 marks by vertex buckets (more
-    than 2^25 vertices), across tree boundaries; every element against the
+    than 2^24 vertices), across tree boundaries; every element against the
     oracle."""
     sizes = np.array([12_000_000, 3, 11_000_000, 1, 10_000_000, 11_000_000, 2], np.int64)
     b = inputs.batch(len(sizes), 1, 1, seed=17, sizes=sizes)
