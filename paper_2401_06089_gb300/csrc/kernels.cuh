@@ -60,6 +60,9 @@ struct OnesweepParams {
     i64 n_trees;
     u32 report_limit = SPIN_LIMIT;   // look-back waits longer than this record ITERATION_LIMIT
     int dbits = 8;         // digit width (9 only for the key-value sort, OS_WRITE_KEYS)
+    // tiles this launch runs (0: all); a pass may be split into launches of
+    // consecutive tile ranges on one stream, the tile counter carried over
+    i64 grid_tiles = 0;
 };
 
 // Digit plan of an LSD sort: pass q sorts by the `width[q]` bits above

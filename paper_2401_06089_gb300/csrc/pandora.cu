@@ -309,8 +309,14 @@ pandora_tuning tuning_snapshot();
 // endpoints' host-to-device copy) only before the first sort pass, which is
 // the first step that reads them; vp_done is recorded once level 0 has
 // written vertex_parent, so its device-to-host copy overlaps the rest.
+constexpr int UV_CHUNKS = 8;
 struct Overlap {
     cudaEvent_t uv_ready = nullptr;
+    // endpoints arriving in chunks of uv_chunk_tiles sort tiles: the first
+    // sort pass runs chunk by chunk, chunk k after uv_chunk[k]
+    int n_uv_chunks = 0;
+    i64 uv_chunk_tiles = 0;
+    const cudaEvent_t *uv_chunk = nullptr;
     cudaEvent_t vp_done = nullptr;
     cudaStream_t vp_stream = nullptr;   // copies vertex_parent to vp_host after vp_done
     i32 *vp_host = nullptr;
@@ -405,7 +411,9 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
     // (pvA starts at a 256-byte boundary: the sort reads these arrays with
     // bulk copies, which need 16-byte aligned sources)
     // the histogram pass read only the weights; the endpoints must be here now
-    if (ov && ov->uv_ready)
+    // (or, arriving in chunks, before each chunk of the first pass)
+    const bool chunked = ov && ov->n_uv_chunks > 0;
+    if (ov && ov->uv_ready && !chunked)
         PANDORA_CUDA(cudaStreamWaitEvent(s, ov->uv_ready, 0));
     u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + ((L.kept_cap + 63) & ~(i64)63);
     u32 *puB = (u32 *)min_word, *pvB = (u32 *)ptr;
@@ -450,7 +458,27 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         }
         PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
-        timer.launch(K_SORT_WEIGHTS, M, [&] { launch_onesweep(flags, P, s); });
+        if (first && chunked) {
+            // consecutive tile ranges, each launched once its endpoints landed
+            const i64 tiles = onesweep_tiles(M);
+            cudaError_t ce = cudaSuccess;
+            timer.launch(K_SORT_WEIGHTS, M, ov->n_uv_chunks, [&] {
+                for (int c = 0; c < ov->n_uv_chunks; ++c) {
+                    const i64 t0 = (i64)c * ov->uv_chunk_tiles;
+                    const i64 t1 = std::min(tiles, t0 + ov->uv_chunk_tiles);
+                    if (t1 <= t0)
+                        continue;
+                    if (ce == cudaSuccess)
+                        ce = cudaStreamWaitEvent(s, ov->uv_chunk[c], 0);
+                    OnesweepParams Pc = P;
+                    Pc.grid_tiles = t1 - t0;
+                    launch_onesweep(flags, Pc, s);
+                }
+            });
+            PANDORA_CUDA(ce);
+        } else {
+            timer.launch(K_SORT_WEIGHTS, M, [&] { launch_onesweep(flags, P, s); });
+        }
         cur_k = P.keys_out;
         cur_v = P.vals_out;
         cur_u = P.pu_out;
@@ -1037,6 +1065,8 @@ int run_pooled(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i
 struct HostIoRes {
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_alloc = nullptr, ev_uv = nullptr, ev_vp = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_w = nullptr;
+    cudaEvent_t ev_chunk[UV_CHUNKS] = {};
 };
 HostIoRes *host_io_res(int dev)
 {
@@ -1050,15 +1080,20 @@ HostIoRes *host_io_res(int dev)
         cudaEventCreateWithFlags(&r.ev_alloc, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&r.ev_uv, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&r.ev_vp, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r.ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&r.ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r.ev_w, cudaEventDisableTiming) != cudaSuccess)
         return nullptr;
+    for (int c = 0; c < UV_CHUNKS; ++c)
+        if (cudaEventCreateWithFlags(&r.ev_chunk[c], cudaEventDisableTiming) != cudaSuccess)
+            return nullptr;
     return &(res[dev] = r);
 }
 
 // One tree from host buffers to host buffers.  Device memory (inputs,
 // outputs, workspace) comes from the library pool on `s`.  The weights go
-// first on `s` (the histogram pass needs only them), the endpoints in
-// parallel on a second stream that the first sort pass waits for;
+// first on `s` (the histogram pass needs only them), then the endpoints on a
+// second stream in eight chunks of whole sort tiles, the first sort pass
+// running over each chunk once it has landed;
 // vertex_parent goes back on a third stream as soon as level 0 has written
 // it, overlapping the other levels, the expansion and the linking;
 // edge_parent follows the last kernel.  Blocking.
@@ -1095,12 +1130,28 @@ int run_host(const i32 *hu, const i32 *hv, const float *hw, i64 M, i32 *hep, i32
             st = PANDORA_ERR_CUDA;
             break;
         }
-        if (M > 0 &&
-            (cudaMemcpyAsync(dw, hw, (size_t)M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-             cudaMemcpyAsync(du, hu, (size_t)M * 4, cudaMemcpyHostToDevice, r->s_in) != cudaSuccess ||
-             cudaMemcpyAsync(dv, hv, (size_t)M * 4, cudaMemcpyHostToDevice, r->s_in) != cudaSuccess)) {
-            st = PANDORA_ERR_CUDA;
-            break;
+        // the weights first (the histogram pass needs only them), then the
+        // endpoints in chunks of whole sort tiles, each chunk's event letting
+        // the first sort pass run over it while the next ones arrive
+        const i64 ct = (onesweep_tiles(M) + UV_CHUNKS - 1) / UV_CHUNKS;
+        if (M > 0) {
+            bool ok = cudaMemcpyAsync(dw, hw, (size_t)M * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                      cudaEventRecord(r->ev_w, s) == cudaSuccess &&
+                      cudaStreamWaitEvent(r->s_in, r->ev_w, 0) == cudaSuccess;
+            for (int c = 0; ok && c < UV_CHUNKS; ++c) {
+                const i64 e0 = std::min<i64>(M, (i64)c * ct * OS_TILE);
+                const i64 e1 = std::min<i64>(M, (i64)(c + 1) * ct * OS_TILE);
+                if (e1 > e0)
+                    ok = cudaMemcpyAsync(du + e0, hu + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice,
+                                         r->s_in) == cudaSuccess &&
+                         cudaMemcpyAsync(dv + e0, hv + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice,
+                                         r->s_in) == cudaSuccess;
+                ok = ok && cudaEventRecord(r->ev_chunk[c], r->s_in) == cudaSuccess;
+            }
+            if (!ok) {
+                st = PANDORA_ERR_CUDA;
+                break;
+            }
         }
         if (cudaEventRecord(r->ev_uv, r->s_in) != cudaSuccess) {
             st = PANDORA_ERR_CUDA;
@@ -1123,6 +1174,9 @@ int run_host(const i32 *hu, const i32 *hv, const float *hw, i64 M, i32 *hep, i32
         }
         Overlap ov;
         ov.uv_ready = r->ev_uv;
+        ov.n_uv_chunks = UV_CHUNKS;
+        ov.uv_chunk_tiles = ct;
+        ov.uv_chunk = r->ev_chunk;
         ov.vp_done = r->ev_vp;
         ov.vp_stream = r->s_out;
         ov.vp_host = hvp;

@@ -670,7 +670,7 @@ static void launch_os(const OnesweepParams &p, cudaStream_t s)
                              (int)bytes);
         done_mask.fetch_or(bit);
     }
-    const i64 tiles = onesweep_tiles(p.n);
+    const i64 tiles = p.grid_tiles > 0 ? p.grid_tiles : onesweep_tiles(p.n);
     onesweep_kernel<F, DBITS><<<(unsigned)tiles, OS_THREADS, bytes, s>>>(p);
 }
 
