@@ -265,6 +265,13 @@ struct LinkParams {
     int n_buckets;
     int2 *rec;             // [m] (edge, parent) pairs by bucket
     u32 *cursor;           // [n_buckets] write cursors, zeroed
+    // the apply pass in apply_parts launches over consecutive bucket ranges
+    // (ids [k * per, (k + 1) * per), per a whole number of buckets), the
+    // event apply_done[k] recorded after launch k; 0 or 1: one launch
+    int apply_parts = 0;
+    cudaEvent_t *apply_done = nullptr;
+    i64 apply_begin = 0;   // record range of one launch (apply_end 0: all)
+    i64 apply_end = 0;
 };
 
 void launch_link(const LinkParams &p, cudaStream_t s);

@@ -3,6 +3,8 @@
 // edge's parent is the next edge of its chain; the heaviest edge of a chain
 // hangs from the chain's head edge p, and the heaviest edge of a root chain
 // is the root (-1).  The result is scattered to the caller's edge order.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 #ifndef PANDORA_LINK_ITEMS
@@ -175,12 +177,13 @@ __global__ void __launch_bounds__(256) link_scatter_kernel(const LinkParams p)
 
 __global__ void __launch_bounds__(256) link_apply_kernel(const LinkParams p)
 {
-    const i64 i0 = (i64)blockIdx.x * (256 * 4) + threadIdx.x;
+    const i64 end = p.apply_end > 0 ? p.apply_end : p.m;
+    const i64 i0 = p.apply_begin + (i64)blockIdx.x * (256 * 4) + threadIdx.x;
     int2 r[4];
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
         const i64 i = i0 + it * 256;
-        r[it] = i < p.m ? p.rec[i] : make_int2(-1, 0);
+        r[it] = i < end ? p.rec[i] : make_int2(-1, 0);
     }
 #pragma unroll
     for (int it = 0; it < 4; ++it)
@@ -200,7 +203,22 @@ void launch_link(const LinkParams &p, cudaStream_t s)
             link_scatter_kernel<true><<<sb, 256, 0, s>>>(p);
         else
             link_scatter_kernel<false><<<sb, 256, 0, s>>>(p);
-        link_apply_kernel<<<(unsigned)((p.m + 1023) / 1024), 256, 0, s>>>(p);
+        if (p.apply_parts <= 1) {
+            link_apply_kernel<<<(unsigned)((p.m + 1023) / 1024), 256, 0, s>>>(p);
+            return;
+        }
+        // bucket ranges applied one launch after another, each followed by
+        // its event (the caller copies that range of edge_parent out)
+        const i64 per = (((i64)p.n_buckets + p.apply_parts - 1) / p.apply_parts) << p.bucket_shift;
+        for (int k = 0; k < p.apply_parts; ++k) {
+            LinkParams q = p;
+            q.apply_begin = std::min(p.m, (i64)k * per);
+            q.apply_end = std::min(p.m, (i64)(k + 1) * per);
+            if (q.apply_end > q.apply_begin)
+                link_apply_kernel<<<(unsigned)((q.apply_end - q.apply_begin + 1023) / 1024), 256, 0, s>>>(q);
+            if (p.apply_done)
+                cudaEventRecord(p.apply_done[k], s);
+        }
         return;
     }
     const unsigned blocks = (unsigned)((p.m + 256 * LINK_ITEMS - 1) / (256 * LINK_ITEMS));

@@ -310,6 +310,7 @@ pandora_tuning tuning_snapshot();
 // the first step that reads them; vp_done is recorded once level 0 has
 // written vertex_parent, so its device-to-host copy overlaps the rest.
 constexpr int UV_CHUNKS = 8;
+constexpr int EP_PARTS = 8;
 struct Overlap {
     cudaEvent_t uv_ready = nullptr;
     // endpoints arriving in chunks of uv_chunk_tiles sort tiles: the first
@@ -317,6 +318,12 @@ struct Overlap {
     int n_uv_chunks = 0;
     i64 uv_chunk_tiles = 0;
     const cudaEvent_t *uv_chunk = nullptr;
+    // edge_parent back to ep_host on vp_stream in EP_PARTS ranges of whole
+    // link buckets, each after its part of the link's apply pass (only where
+    // the link is bucketed; *ep_copied then tells the caller)
+    i32 *ep_host = nullptr;
+    cudaEvent_t *ep_done = nullptr;
+    bool *ep_copied = nullptr;
     cudaEvent_t vp_done = nullptr;
     cudaStream_t vp_stream = nullptr;   // copies vertex_parent to vp_host after vp_done
     i32 *vp_host = nullptr;
@@ -759,8 +766,27 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         else
             PANDORA_CUDA(cudaMemsetAsync(ctrl->link_cursor, 0, sizeof(ctrl->link_cursor), s));
     }
-    timer.launch(K_LINK, M, K.n_buckets > 0 ? 2 : 1, [&] { launch_link(K, s); });
+    const bool ep_parts = ov && ov->ep_host && ov->ep_done && ov->vp_stream && K.n_buckets > 0;
+    if (ep_parts) {
+        K.apply_parts = EP_PARTS;
+        K.apply_done = ov->ep_done;
+    }
+    timer.launch(K_LINK, M, K.n_buckets > 0 ? 1 + (ep_parts ? EP_PARTS : 1) : 1,
+                 [&] { launch_link(K, s); });
     PANDORA_CUDA(cudaGetLastError());
+    if (ep_parts) {
+        // the same bucket ranges as the apply launches
+        const i64 per = (((i64)K.n_buckets + EP_PARTS - 1) / EP_PARTS) << K.bucket_shift;
+        for (int k = 0; k < EP_PARTS; ++k) {
+            const i64 b = std::min(M, (i64)k * per), e = std::min(M, (i64)(k + 1) * per);
+            PANDORA_CUDA(cudaStreamWaitEvent(ov->vp_stream, ov->ep_done[k], 0));
+            if (e > b)
+                PANDORA_CUDA(cudaMemcpyAsync(ov->ep_host + b, ep + b, (size_t)(e - b) * 4,
+                                             cudaMemcpyDeviceToHost, ov->vp_stream));
+        }
+        if (ov->ep_copied)
+            *ov->ep_copied = true;
+    }
     if (!blocking)
         return PANDORA_OK;
     if (int e = read_counters(ctrl, &h, s))
@@ -1067,6 +1093,7 @@ struct HostIoRes {
     cudaEvent_t ev_alloc = nullptr, ev_uv = nullptr, ev_vp = nullptr, ev_out = nullptr;
     cudaEvent_t ev_w = nullptr;
     cudaEvent_t ev_chunk[UV_CHUNKS] = {};
+    cudaEvent_t ev_ep[EP_PARTS] = {};
 };
 HostIoRes *host_io_res(int dev)
 {
@@ -1086,6 +1113,9 @@ HostIoRes *host_io_res(int dev)
     for (int c = 0; c < UV_CHUNKS; ++c)
         if (cudaEventCreateWithFlags(&r.ev_chunk[c], cudaEventDisableTiming) != cudaSuccess)
             return nullptr;
+    for (int c = 0; c < EP_PARTS; ++c)
+        if (cudaEventCreateWithFlags(&r.ev_ep[c], cudaEventDisableTiming) != cudaSuccess)
+            return nullptr;
     return &(res[dev] = r);
 }
 
@@ -1096,7 +1126,9 @@ HostIoRes *host_io_res(int dev)
 // running over each chunk once it has landed;
 // vertex_parent goes back on a third stream as soon as level 0 has written
 // it, overlapping the other levels, the expansion and the linking;
-// edge_parent follows the last kernel.  Blocking.
+// edge_parent follows on that stream range by range as the bucketed link
+// finishes each range of caller ids (after the last kernel when the link is
+// not bucketed).  Blocking.
 int run_host(const i32 *hu, const i32 *hv, const float *hw, i64 M, i32 *hep, i32 *hvp,
              cudaStream_t s)
 {
@@ -1177,13 +1209,17 @@ int run_host(const i32 *hu, const i32 *hv, const float *hw, i64 M, i32 *hep, i32
         ov.n_uv_chunks = UV_CHUNKS;
         ov.uv_chunk_tiles = ct;
         ov.uv_chunk = r->ev_chunk;
+        bool ep_copied = false;
+        ov.ep_host = hep;
+        ov.ep_done = r->ev_ep;
+        ov.ep_copied = &ep_copied;
         ov.vp_done = r->ev_vp;
         ov.vp_stream = r->s_out;
         ov.vp_host = hvp;
         st = run_core(du, dv, dw, M, 1, nullptr, dep, dvp, ws, ws_bytes, nullptr, s, true, &ov);
         if (st != PANDORA_OK)
             break;
-        if (M > 0 &&
+        if (M > 0 && !ep_copied &&
             cudaMemcpyAsync(hep, dep, (size_t)M * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
             st = PANDORA_ERR_CUDA;
             break;

@@ -1,5 +1,7 @@
 """The host-buffer entry point (pandora_dendrogram_host): host arrays in, host
 arrays out, copies overlapped with the path; every element against the oracle."""
+import os
+
 import numpy as np
 import pytest
 
@@ -64,3 +66,16 @@ def test_host_rejects_device_tensors(pd):
     with pytest.raises(ValueError):
         pd.dendrogram_host(torch.from_numpy(t.u).cuda(), torch.from_numpy(t.v),
                            torch.from_numpy(t.w))
+
+
+def test_host_above_bucketed_link_threshold(pd):
+    """4*10^7 edges (above 2^25): the link stores edge_parent by caller-id
+    buckets, and the host entry point copies edge_parent back range by range
+    as the apply pass finishes each range of buckets; the endpoints arrive in
+    chunks that the first sort pass takes one by one.  Every element against
+    the oracle."""
+    t = inputs.rrt(40_000_001, 8)
+    ep, vp = _host(pd, t, pinned=True)
+    oep, ovp = oracle.dendrogram_threads(t.u, t.v, t.w, os.cpu_count() or 1)
+    np.testing.assert_array_equal(vp, ovp)
+    np.testing.assert_array_equal(ep, oep)
