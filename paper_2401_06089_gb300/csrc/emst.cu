@@ -7,8 +7,10 @@
 //   2. linear BVH over the sorted points (Karras 2012): internal node i
 //      spans the key range whose longest common prefix it owns; equal codes
 //      are told apart by their position
-//   3. bottom-up refit of every internal node: box, least core2 below it,
-//      and the component of its points when they all share one (else -1)
+//   3. bottom-up refit: every internal node keeps, for each of its two
+//      children, the box, the least core2 below it and the component of
+//      its points when they all share one (else -1), so that a traversal
+//      step reads one 64-byte record and needs no point record for a leaf
 //   4. core2 of every point: k nearest points by a best-first traversal with
 //      the k smallest squared distances in a sorted list
 //   5. Boruvka rounds: every point finds its least edge, in the (mr2, smaller
@@ -162,7 +164,7 @@ __device__ __forceinline__ int em_delta(const u32 *__restrict__ k, i64 n, i64 i,
 }
 
 __global__ void __launch_bounds__(256) em_build_kernel(const u32 *__restrict__ k, i64 n,
-                                                       int *left, int *right, int *parent)
+                                                       int2 *kids, int *parent)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1)
@@ -190,8 +192,7 @@ __global__ void __launch_bounds__(256) em_build_kernel(const u32 *__restrict__ k
     const i64 lo = i < j ? i : j, hi = i < j ? j : i;
     const int lc = (int)(lo == gamma ? (n - 1) + gamma : gamma);
     const int rc = (int)(hi == gamma + 1 ? (n - 1) + gamma + 1 : gamma + 1);
-    left[i] = lc;
-    right[i] = rc;
+    kids[i] = make_int2(lc, rc);
     parent[lc] = (int)i;
     parent[rc] = (int)i;
     if (i == 0)
@@ -199,30 +200,38 @@ __global__ void __launch_bounds__(256) em_build_kernel(const u32 *__restrict__ k
 }
 
 // ---- 3. bottom-up refit ------------------------------------------------------------
-// nlo[i] = (box lo, least core2), nhi[i] = (box hi, component as int bits or -1)
-struct NodeData {
-    float4 lo, hi;
+// Every internal node keeps the boxes of both its children (wide node): lo =
+// (box lo, least core2 below), hi = (box hi, component of all points below
+// as int bits, or -1).  A leaf child's box is its point (xyz, core2) with the
+// point's component, so a traversal reads one 64-byte record per visited
+// node and no point record at all for a leaf child.
+struct WideNode {
+    float4 lo[2];
+    float4 hi[2];
 };
 
-__device__ __forceinline__ NodeData em_child(i64 n, int c, const float4 *P4, const i32 *comp,
-                                             const float4 *nlo, const float4 *nhi)
+// Box of node c (leaf: its point), from data written earlier in this launch
+// by other threads (read past L1).
+__device__ __forceinline__ void em_box_of(i64 n, int c, const float4 *P4, const i32 *comp,
+                                          const WideNode *wn, float4 &lo, float4 &hi)
 {
-    NodeData r;
     if (c >= n - 1) {
         const float4 p = __ldcg(P4 + (c - (n - 1)));
-        r.lo = p;
-        r.hi = make_float4(p.x, p.y, p.z, __int_as_float(__ldcg(comp + (c - (n - 1)))));
+        lo = p;
+        hi = make_float4(p.x, p.y, p.z, __int_as_float(__ldcg(comp + (c - (n - 1)))));
     } else {
-        r.lo = __ldcg(nlo + c);
-        r.hi = __ldcg(nhi + c);
+        const float4 a0 = __ldcg(&wn[c].lo[0]), a1 = __ldcg(&wn[c].lo[1]);
+        const float4 b0 = __ldcg(&wn[c].hi[0]), b1 = __ldcg(&wn[c].hi[1]);
+        const int c0 = __float_as_int(b0.w), c1 = __float_as_int(b1.w);
+        lo = make_float4(fminf(a0.x, a1.x), fminf(a0.y, a1.y), fminf(a0.z, a1.z), fminf(a0.w, a1.w));
+        hi = make_float4(fmaxf(b0.x, b1.x), fmaxf(b0.y, b1.y), fmaxf(b0.z, b1.z),
+                         __int_as_float(c0 == c1 ? c0 : -1));
     }
-    return r;
 }
 
 __global__ void __launch_bounds__(256) em_refit_kernel(i64 n, const float4 *P4, const i32 *comp,
-                                                       const int *left, const int *right,
-                                                       const int *parent, float4 *nlo,
-                                                       float4 *nhi, int *flags, int *status)
+                                                       const int2 *kids, const int *parent,
+                                                       WideNode *wn, int *flags, int *status)
 {
     const i64 j = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n)
@@ -237,13 +246,14 @@ __global__ void __launch_bounds__(256) em_refit_kernel(i64 n, const float4 *P4, 
         if (atomicAdd(flags + node, 1) == 0)
             return;   // the other child is not done yet; its thread goes on
         __threadfence();
-        const NodeData a = em_child(n, left[node], P4, comp, nlo, nhi);
-        const NodeData b = em_child(n, right[node], P4, comp, nlo, nhi);
-        const int ca = __float_as_int(a.hi.w), cb = __float_as_int(b.hi.w);
-        nlo[node] = make_float4(fminf(a.lo.x, b.lo.x), fminf(a.lo.y, b.lo.y),
-                                fminf(a.lo.z, b.lo.z), fminf(a.lo.w, b.lo.w));
-        nhi[node] = make_float4(fmaxf(a.hi.x, b.hi.x), fmaxf(a.hi.y, b.hi.y),
-                                fmaxf(a.hi.z, b.hi.z), __int_as_float(ca == cb ? ca : -1));
+        const int2 ch = kids[node];
+        float4 l0, h0, l1, h1;
+        em_box_of(n, ch.x, P4, comp, wn, l0, h0);
+        em_box_of(n, ch.y, P4, comp, wn, l1, h1);
+        wn[node].lo[0] = l0;
+        wn[node].hi[0] = h0;
+        wn[node].lo[1] = l1;
+        wn[node].hi[1] = h1;
         node = parent[node];
     }
 }
@@ -293,10 +303,8 @@ struct TopK {
 #endif
 template <int KCAP>
 __global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n, int k, const float4 *__restrict__ P4,
-                                                     const int *__restrict__ left,
-                                                     const int *__restrict__ right,
-                                                     const float4 *__restrict__ nlo,
-                                                     const float4 *__restrict__ nhi, float *core2,
+                                                     const int2 *__restrict__ kids,
+                                                     const WideNode *__restrict__ wn, float *core2,
                                                      int *status)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,26 +321,34 @@ __global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n,
         return;
     }
     float kth = best.kth(k);
+    // a node goes on the stack with its box's lower bound, taken again
+    // against the k-th distance when it is popped
     int stack[EM_STACK];
+    float slb[EM_STACK];
     int sp = 0;
-    stack[sp++] = 0;
+    stack[0] = 0;
+    slb[0] = 0.f;
+    sp = 1;
     while (sp > 0) {
-        const int node = stack[--sp];
-        if (em_box_d2(q, nlo[node], nhi[node]) >= kth)
+        --sp;
+        if (slb[sp] >= kth)
             continue;
-        int ch[2] = {left[node], right[node]};
+        const int node = stack[sp];
+        const int2 kc = kids[node];
+        const int ch[2] = {kc.x, kc.y};
         float lb[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
+            const float4 clo = wn[node].lo[c];
             lb[c] = INFINITY;
             if (ch[c] >= n - 1) {
                 const i64 j = ch[c] - (n - 1);
                 if (j < w0 || j > w1) {   // the window's points are counted already
-                    best.insert(em_d2(q, P4[j]), k);
+                    best.insert(em_d2(q, clo), k);
                     kth = best.kth(k);
                 }
             } else {
-                lb[c] = em_box_d2(q, nlo[ch[c]], nhi[ch[c]]);
+                lb[c] = em_box_d2(q, clo, wn[node].hi[c]);
             }
         }
         // push the farther child first so that the nearer one is visited next
@@ -346,7 +362,9 @@ __global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n,
                     sp = 0;
                     break;
                 }
-                stack[sp++] = ch[c];
+                stack[sp] = ch[c];
+                slb[sp] = lb[c];
+                ++sp;
             }
         }
     }
@@ -377,10 +395,8 @@ __device__ __forceinline__ float em_comp_bound(const u32 *cbest_w, int c)
 __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i64 n, const float4 *__restrict__ P4,
                                                        const i32 *__restrict__ comp,
                                                        const u32 *__restrict__ orig,
-                                                       const int *__restrict__ left,
-                                                       const int *__restrict__ right,
-                                                       const float4 *__restrict__ nlo,
-                                                       const float4 *__restrict__ nhi,
+                                                       const int2 *__restrict__ kids,
+                                                       const WideNode *__restrict__ wn,
                                                        u32 *cbest_w, float *qbw, u32 *qlo,
                                                        u32 *qhi, int *status)
 {
@@ -396,42 +412,45 @@ __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i6
     // every edge of q weighs at least core2(q): above the component's least
     // edge found so far, q cannot supply it
     if (!(q.w > cw)) {
+        // a node goes on the stack with the lower bound of its box (no subtree
+        // wholly in q's component is pushed), taken again against the bound
+        // when it is popped
         int stack[EM_STACK];
-        int sp = 0;
-        stack[sp++] = 0;
+        float slb[EM_STACK];
+        stack[0] = 0;
+        slb[0] = 0.f;
+        int sp = 1;
         int pops = 0;
         while (sp > 0) {
-            const int node = stack[--sp];
+            --sp;
             if ((++pops & 15) == 0)
                 cw = em_comp_bound(cbest_w, cq);
-            const float bound = fminf(bw, cw);
-            const float4 lo = nlo[node], hi = nhi[node];
-            if (__float_as_int(hi.w) == cq)
-                continue;   // all of its points are in q's component
-            if (fmaxf(fmaxf(q.w, lo.w), em_box_d2(q, lo, hi)) > bound)
+            if (slb[sp] > fminf(bw, cw))
                 continue;
-            const int ch[2] = {left[node], right[node]};
+            const int node = stack[sp];
+            const int2 kc = kids[node];
+            const int ch[2] = {kc.x, kc.y};
             float lb[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 lb[c] = INFINITY;
+                const float4 clo = wn[node].lo[c], chi = wn[node].hi[c];
+                if (__float_as_int(chi.w) == cq)
+                    continue;   // all of its points are in q's component
                 if (ch[c] >= n - 1) {
-                    const int j = ch[c] - (int)(n - 1);
-                    if (comp[j] == cq)
-                        continue;
-                    const float4 p = P4[j];
-                    const float w2 = fmaxf(fmaxf(q.w, p.w), em_d2(q, p));
-                    const u32 oj = orig[j];
-                    const u32 lo_id = oq < oj ? oq : oj, hi_id = oq < oj ? oj : oq;
-                    if (em_less(w2, lo_id, hi_id, bw, blo, bhi)) {
-                        bw = w2;
-                        blo = lo_id;
-                        bhi = hi_id;
+                    // a point of another component: clo = (x, y, z, core2)
+                    const float w2 = fmaxf(fmaxf(q.w, clo.w), em_d2(q, clo));
+                    if (w2 <= bw) {
+                        const u32 oj = orig[ch[c] - (n - 1)];
+                        const u32 lo_id = oq < oj ? oq : oj, hi_id = oq < oj ? oj : oq;
+                        if (em_less(w2, lo_id, hi_id, bw, blo, bhi)) {
+                            bw = w2;
+                            blo = lo_id;
+                            bhi = hi_id;
+                        }
                     }
                 } else {
-                    const float4 clo = nlo[ch[c]], chi = nhi[ch[c]];
-                    if (__float_as_int(chi.w) != cq)
-                        lb[c] = fmaxf(fmaxf(q.w, clo.w), em_box_d2(q, clo, chi));
+                    lb[c] = fmaxf(fmaxf(q.w, clo.w), em_box_d2(q, clo, chi));
                 }
             }
             const float bound2 = fminf(bw, cw);
@@ -447,7 +466,9 @@ __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i6
                         sp = 0;
                         break;
                     }
-                    stack[sp++] = ch[c];
+                    stack[sp] = ch[c];
+                    slb[sp] = lb[c];
+                    ++sp;
                 }
             }
         }
@@ -600,7 +621,7 @@ inline unsigned blocks_for(i64 n, int t) { return (unsigned)std::max<i64>(1, (n 
 
 struct EmLayout {
     size_t ctrl, codesA, codesB, idsA, idsB, lb, P4, pos_of, comp, parentc, cbest_w, cbest_e;
-    size_t qbw, qlo, qhi, eu, ev, ew2, core2, left, right, nparent, nlo, nhi, flags, total;
+    size_t qbw, qlo, qhi, eu, ev, ew2, core2, kids, nparent, wn, flags, total;
 };
 
 EmLayout em_layout(i64 n)
@@ -632,11 +653,9 @@ EmLayout em_layout(i64 n)
     L.ev = take(n * 4);
     L.ew2 = take(n * 4);
     L.core2 = take(n * 4);
-    L.left = take(ni * 4);
-    L.right = take(ni * 4);
+    L.kids = take(ni * 8);
     L.nparent = take((2 * n) * 4);
-    L.nlo = take(ni * 16);
-    L.nhi = take(ni * 16);
+    L.wn = take(ni * sizeof(WideNode));
     L.flags = take(ni * 4);
     L.total = off;
     return L;
@@ -672,9 +691,9 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
     u32 *qlo = (u32 *)(base + L.qlo), *qhi = (u32 *)(base + L.qhi);
     u32 *eu = (u32 *)(base + L.eu), *ev = (u32 *)(base + L.ev);
     float *ew2 = (float *)(base + L.ew2), *core2 = (float *)(base + L.core2);
-    int *left = (int *)(base + L.left), *right = (int *)(base + L.right);
+    int2 *kids = (int2 *)(base + L.kids);
     int *nparent = (int *)(base + L.nparent);
-    float4 *nlo = (float4 *)(base + L.nlo), *nhi = (float4 *)(base + L.nhi);
+    WideNode *wn = (WideNode *)(base + L.wn);
     int *flags = (int *)(base + L.flags);
     EmCtrl h{};
 
@@ -722,20 +741,18 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
     em_gather_kernel<<<blocks_for(n, 256), 256, 0, s>>>(pts, n, cv, P4, pos_of, comp);
     const u32 *orig = cv;
     if (n > 1) {
-        em_build_kernel<<<blocks_for(n - 1, 256), 256, 0, s>>>(ck, n, left, right, nparent);
+        em_build_kernel<<<blocks_for(n - 1, 256), 256, 0, s>>>(ck, n, kids, nparent);
         EM_CUDA(cudaMemsetAsync(flags, 0, (size_t)(n - 1) * 4, s));
-        em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, left, right, nparent, nlo,
-                                                           nhi, flags, &ctrl->status);
+        em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, kids, nparent, wn, flags,
+                                                           &ctrl->status);
     }
     if (k <= 8)
-        em_knn_kernel<8><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi, core2,
-                                                            &ctrl->status);
+        em_knn_kernel<8><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, kids, wn, core2, &ctrl->status);
     else if (k <= 16)
-        em_knn_kernel<16><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi,
-                                                             core2, &ctrl->status);
+        em_knn_kernel<16><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, kids, wn, core2, &ctrl->status);
     else
-        em_knn_kernel<EM_K_MAX><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, left, right, nlo, nhi,
-                                                                   core2, &ctrl->status);
+        em_knn_kernel<EM_K_MAX><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, kids, wn, core2,
+                                                                   &ctrl->status);
     em_set_core_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, core2);
     em_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(cbest_w, cbest_e, n);
     EM_CUDA(cudaGetLastError());
@@ -743,12 +760,11 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
         if (round >= EM_MAX_ROUNDS)
             return PANDORA_ERR_ITERATION_LIMIT;
         EM_CUDA(cudaMemsetAsync(flags, 0, (size_t)(n - 1) * 4, s));
-        em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, left, right, nparent, nlo,
-                                                           nhi, flags, &ctrl->status);
-        em_seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, cbest_w);
-        em_query_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, P4, comp, orig, left, right, nlo,
-                                                           nhi, cbest_w, qbw, qlo, qhi,
+        em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, kids, nparent, wn, flags,
                                                            &ctrl->status);
+        em_seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, cbest_w);
+        em_query_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, P4, comp, orig, kids, wn, cbest_w,
+                                                           qbw, qlo, qhi, &ctrl->status);
         em_choose_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, comp, cbest_w, qbw, qlo, qhi,
                                                             cbest_e);
         em_link_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, comp, pos_of, cbest_w, cbest_e,
