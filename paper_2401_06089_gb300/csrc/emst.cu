@@ -313,14 +313,22 @@ __global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n,
     const float4 q = P4[i];
     TopK<KCAP> best;
     best.init();
+    // a distance at or above the k-th smallest so far cannot enter the
+    // first k slots (the insertion is strict), so only smaller ones are
+    // inserted
     const i64 w0 = i - k < 0 ? 0 : i - k, w1 = i + k >= n ? n - 1 : i + k;
-    for (i64 j = w0; j <= w1; ++j)
-        best.insert(em_d2(q, P4[j]), k);
+    float kth = INFINITY;
+    for (i64 j = w0; j <= w1; ++j) {
+        const float d2 = em_d2(q, P4[j]);
+        if (d2 < kth) {
+            best.insert(d2, k);
+            kth = best.kth(k);
+        }
+    }
     if (n == 1) {
-        core2[i] = best.kth(k);
+        core2[i] = kth;
         return;
     }
-    float kth = best.kth(k);
     // a node goes on the stack with its box's lower bound, taken again
     // against the k-th distance when it is popped
     int stack[EM_STACK];
@@ -344,8 +352,11 @@ __global__ void __launch_bounds__(128, PANDORA_EM_KNN_MINB) em_knn_kernel(i64 n,
             if (ch[c] >= n - 1) {
                 const i64 j = ch[c] - (n - 1);
                 if (j < w0 || j > w1) {   // the window's points are counted already
-                    best.insert(em_d2(q, clo), k);
-                    kth = best.kth(k);
+                    const float d2 = em_d2(q, clo);
+                    if (d2 < kth) {
+                        best.insert(d2, k);
+                        kth = best.kth(k);
+                    }
                 }
             } else {
                 lb[c] = em_box_d2(q, clo, wn[node].hi[c]);
@@ -389,6 +400,20 @@ __device__ __forceinline__ float em_comp_bound(const u32 *cbest_w, int c)
     return __uint_as_float(*(const volatile u32 *)(cbest_w + c));
 }
 
+// A point's least edge of the previous round (weight pw, id pair lo < hi,
+// one of them the point's own id oq) is still an edge to another component
+// when its far end has not joined the point's component since: components
+// only merge, so it stays a candidate and bounds the point's least edge
+// from above.
+__device__ __forceinline__ bool em_prev_valid(float pw, u32 lo, u32 hi, u32 oq, int cq,
+                                              const i32 *comp, const i32 *pos_of)
+{
+    if (!(pw < INFINITY))
+        return false;
+    const u32 other = lo == oq ? hi : lo;
+    return comp[pos_of[other]] != cq;
+}
+
 #ifndef PANDORA_EM_QUERY_MINB
 #define PANDORA_EM_QUERY_MINB 1
 #endif
@@ -397,6 +422,7 @@ __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i6
                                                        const u32 *__restrict__ orig,
                                                        const int2 *__restrict__ kids,
                                                        const WideNode *__restrict__ wn,
+                                                       const i32 *__restrict__ pos_of,
                                                        u32 *cbest_w, float *qbw, u32 *qlo,
                                                        u32 *qhi, int *status)
 {
@@ -408,6 +434,15 @@ __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i6
     const u32 oq = orig[i];
     float bw = INFINITY;
     u32 blo = 0xFFFFFFFFu, bhi = 0xFFFFFFFFu;
+    {
+        const float pw = qbw[i];
+        const u32 plo = qlo[i], phi = qhi[i];
+        if (em_prev_valid(pw, plo, phi, oq, cq, comp, pos_of)) {
+            bw = pw;
+            blo = plo;
+            bhi = phi;
+        }
+    }
     float cw = em_comp_bound(cbest_w, cq);
     // every edge of q weighs at least core2(q): above the component's least
     // edge found so far, q cannot supply it
@@ -488,7 +523,11 @@ __global__ void __launch_bounds__(128, PANDORA_EM_QUERY_MINB) em_query_kernel(i6
 constexpr int EM_SEED = 8;
 __global__ void __launch_bounds__(256) em_seed_kernel(i64 n, const float4 *__restrict__ P4,
                                                       const i32 *__restrict__ comp,
-                                                      u32 *cbest_w)
+                                                      const u32 *__restrict__ orig,
+                                                      const i32 *__restrict__ pos_of,
+                                                      const float *__restrict__ qbw,
+                                                      const u32 *__restrict__ qlo,
+                                                      const u32 *__restrict__ qhi, u32 *cbest_w)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
@@ -503,6 +542,10 @@ __global__ void __launch_bounds__(256) em_seed_kernel(i64 n, const float4 *__res
         const float4 p = P4[j];
         bw = fminf(bw, fmaxf(fmaxf(q.w, p.w), em_d2(q, p)));
     }
+    // and the point's least edge of the previous round, if still valid
+    const float pw = qbw[i];
+    if (pw < bw && em_prev_valid(pw, qlo[i], qhi[i], orig[i], cq, comp, pos_of))
+        bw = pw;
     if (bw < INFINITY && __float_as_uint(bw) < *(const volatile u32 *)(cbest_w + cq))
         atomicMin(cbest_w + cq, __float_as_uint(bw));
 }
@@ -608,12 +651,13 @@ __global__ void __launch_bounds__(256) em_output_kernel(i64 n, const u32 *eu, co
         core_out[orig[i]] = core2[i];
 }
 
-__global__ void em_fill_kernel(u32 *a, u64 *b, i64 n)
+__global__ void em_fill_kernel(u32 *a, u64 *b, float *qbw, i64 n)
 {
     const i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         a[i] = INF_BITS;
         b[i] = ~0ull;
+        qbw[i] = INFINITY;
     }
 }
 
@@ -754,7 +798,7 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
         em_knn_kernel<EM_K_MAX><<<blocks_for(n, 128), 128, 0, s>>>(n, k, P4, kids, wn, core2,
                                                                    &ctrl->status);
     em_set_core_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, core2);
-    em_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(cbest_w, cbest_e, n);
+    em_fill_kernel<<<blocks_for(n, 256), 256, 0, s>>>(cbest_w, cbest_e, qbw, n);
     EM_CUDA(cudaGetLastError());
     for (int round = 0; n > 1; ++round) {
         if (round >= EM_MAX_ROUNDS)
@@ -762,9 +806,10 @@ int em_run(const float *pts, i64 n, int k, i32 *u, i32 *v, float *w, float *core
         EM_CUDA(cudaMemsetAsync(flags, 0, (size_t)(n - 1) * 4, s));
         em_refit_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, kids, nparent, wn, flags,
                                                            &ctrl->status);
-        em_seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, cbest_w);
-        em_query_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, P4, comp, orig, kids, wn, cbest_w,
-                                                           qbw, qlo, qhi, &ctrl->status);
+        em_seed_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, P4, comp, orig, pos_of, qbw, qlo,
+                                                          qhi, cbest_w);
+        em_query_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, P4, comp, orig, kids, wn, pos_of,
+                                                           cbest_w, qbw, qlo, qhi, &ctrl->status);
         em_choose_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, comp, cbest_w, qbw, qlo, qhi,
                                                             cbest_e);
         em_link_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, comp, pos_of, cbest_w, cbest_e,
