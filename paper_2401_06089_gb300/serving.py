@@ -170,7 +170,10 @@ class DendrogramServer:
             v = torch.cat([r.v for r in reqs]) if m else torch.empty_like(u)
             w = torch.cat([r.w for r in reqs]) if m else torch.empty(0, dtype=torch.float32,
                                                                      device=self.device)
-            off = torch.tensor(offsets, dtype=torch.int64).to(self.device, non_blocking=True)
+            # offsets from pinned memory: an asynchronous copy that does not
+            # wait for the stream (kept alive until the batch retires)
+            off_h = torch.tensor(offsets, dtype=torch.int64).pin_memory()
+            off = off_h.to(self.device, non_blocking=True)
             ws = torch.empty(B.workspace_size(m, max(t, 1)), dtype=torch.uint8, device=self.device)
             ep = torch.empty(m, dtype=torch.int32, device=self.device)
             vp = torch.empty(m + t, dtype=torch.int32, device=self.device)
@@ -179,7 +182,7 @@ class DendrogramServer:
             ev.record(stream)
         self.bytes_in_use += fp
         self.inflight.append(_Batch(self._next_bid, reqs, stream, ev, ws, ep, vp, offsets, fp,
-                                    t_admit, keep=[u, v, w, off]))
+                                    t_admit, keep=[u, v, w, off, off_h]))
         self._next_bid += 1
         self.max_inflight = max(self.max_inflight, len(self.inflight))
 
