@@ -40,10 +40,8 @@ struct OnesweepParams {
     const u32 *vals_in;
     u32 *keys_out;
     u32 *vals_out;
-    const u32 *pu_in;      // carried endpoints (OS_PAYLOAD_UV, later passes)
-    const u32 *pv_in;
-    u32 *pu_out;
-    u32 *pv_out;
+    const int2 *uv_in;     // carried endpoints (OS_PAYLOAD_UV, later passes)
+    int2 *uv_out;          // carried endpoints out; on the last pass the level-0 edges
     i64 n;
     int shift;
     const u32 *hist;       // [256] digit counts of this pass
@@ -54,7 +52,6 @@ struct OnesweepParams {
     // caller endpoints (first pass) and level-0 output (last pass)
     const i32 *u;
     const i32 *v;
-    int2 *ab_out;
     i64 n_vertices;
     const i64 *edge_off;   // OS_FOREST
     i64 n_trees;

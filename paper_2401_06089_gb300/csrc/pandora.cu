@@ -412,19 +412,17 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         if (passes.empty())
             passes.push_back(3);   // still one pass: it writes the permutation and endpoints
     }
-    // the endpoint streams ping-pong through arrays that are idle until the
-    // level loop: the two halves of kept_rec (>= M entries each), min_word
-    // (2N entries) and ptr (N)
-    // (pvA starts at a 256-byte boundary: the sort reads these arrays with
-    // bulk copies, which need 16-byte aligned sources)
+    // the endpoint stream (an int2 per edge) ping-pongs through arrays that
+    // are idle until the level loop: kept_rec (>= M int2) and min_word (N
+    // words of 8 bytes), both 256-byte aligned as the sort's bulk copies need
     // the histogram pass read only the weights; the endpoints must be here now
     // (or, arriving in chunks, before each chunk of the first pass)
     const bool chunked = ov && ov->n_uv_chunks > 0;
     if (ov && ov->uv_ready && !chunked)
         PANDORA_CUDA(cudaStreamWaitEvent(s, ov->uv_ready, 0));
-    u32 *puA = (u32 *)kept_rec, *pvA = (u32 *)kept_rec + ((L.kept_cap + 63) & ~(i64)63);
-    u32 *puB = (u32 *)min_word, *pvB = (u32 *)ptr;
-    const u32 *cur_k = nullptr, *cur_v = nullptr, *cur_u = nullptr, *cur_w = nullptr;
+    int2 *uvA = (int2 *)kept_rec, *uvB = (int2 *)min_word;
+    const u32 *cur_k = nullptr, *cur_v = nullptr;
+    const int2 *cur_uv = nullptr;
     bool toA = false;
     for (size_t k = 0; k < passes.size(); ++k) {
         const bool first = k == 0, last = k + 1 == passes.size();
@@ -449,19 +447,17 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         } else {
             P.keys_in = cur_k;
             P.vals_in = cur_v;
-            P.pu_in = cur_u;
-            P.pv_in = cur_w;
+            P.uv_in = cur_uv;
         }
         if (last) {
             flags |= OS_LAST_AB;
             P.vals_out = perm;
-            P.ab_out = ab0;
+            P.uv_out = ab0;
         } else {
             flags |= OS_WRITE_KEYS;
             P.keys_out = toA ? keysA : keysB;
             P.vals_out = toA ? valsA : valsB;
-            P.pu_out = toA ? puA : puB;
-            P.pv_out = toA ? pvA : pvB;
+            P.uv_out = toA ? uvA : uvB;
         }
         PANDORA_CUDA(cudaMemsetAsync(lb, 0, (size_t)onesweep_tiles(M) * RADIX * 8, s));
         PANDORA_CUDA(cudaMemsetAsync(&ctrl->tile_counter[0], 0, 4, s));
@@ -488,8 +484,7 @@ int run_core(const i32 *u, const i32 *v, const float *w, i64 M, i64 T, const i64
         }
         cur_k = P.keys_out;
         cur_v = P.vals_out;
-        cur_u = P.pu_out;
-        cur_w = P.pv_out;
+        cur_uv = P.uv_out;
         toA = !toA;
     }
     PANDORA_CUDA(cudaGetLastError());

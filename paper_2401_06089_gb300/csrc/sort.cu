@@ -21,7 +21,8 @@
 // digit totals come from one histogram read of all keys before the first
 // pass.
 //
-// The weight sort carries the endpoints (u, v) as two extra value streams:
+// The weight sort carries the endpoints (u, v) as one extra 8-byte value
+// stream (int2; the first pass pairs the caller's two arrays):
 // moving 8 more bytes per edge through each pass is cheaper than gathering
 // them at random afterwards (a random 4-byte read costs a 64-byte DRAM
 // burst).
@@ -242,7 +243,6 @@ __global__ void __launch_bounds__(OS_THREADS,
                                   (FLAGS & OS_PAYLOAD_UV) || DBITS > 9 ? OS_MIN_BLOCKS : OS_MIN_BLOCKS + 1)
     onesweep_kernel(const OnesweepParams p)
 {
-    constexpr bool kAB = (FLAGS & OS_LAST_AB) != 0;
     constexpr bool kUV = (FLAGS & OS_PAYLOAD_UV) != 0;
     constexpr bool kGen = (FLAGS & OS_GEN_VALS) != 0;
     using L = OsSmem<FLAGS, DBITS>;
@@ -252,11 +252,17 @@ __global__ void __launch_bounds__(OS_THREADS,
     constexpr int DPT = DigitsPerThread<RD>::value;   // digits owned per thread
     constexpr int ACT = RD / DPT;                      // threads that own digits
     extern __shared__ __align__(128) unsigned char smem[];
-    u32 *B0 = (u32 *)smem;                        // keys in; later values in digit order
-    u32 *B1 = B0 + OS_TILE;                       // values in; later u in digit order
-    u32 *B2 = B1 + OS_TILE;                       // u in (kUV)
-    u32 *B3 = B2 + OS_TILE;                       // v in (kUV)
-    u32 *B4 = kUV ? B3 + OS_TILE : B2;            // keys in digit order; later v
+    // B0 keys in, later values in digit order; B1 values in; B2 keys in
+    // digit order; with endpoints (kUV) B3..B4 the endpoints in (the first
+    // pass: u in B3 and v in B4 from the caller's arrays; later passes one
+    // int2 per element) and B1..B2, once values and keys are out, the
+    // endpoints in digit order (int2)
+    u32 *B0 = (u32 *)smem;
+    u32 *B1 = B0 + OS_TILE;
+    u32 *B2 = B1 + OS_TILE;
+    u32 *B3 = B2 + OS_TILE;
+    u32 *B4 = B3 + OS_TILE;                       // kUV only
+    u32 *KD = B2;                                 // keys in digit order
     WH (*s_whist)[RD] = (WH(*)[RD])(smem + L::kWhist);
     unsigned char *s_dig = smem + L::kDig;        // 8-bit digits only
     __shared__ u32 s_goff[RD];                    // global position of local position 0, per digit
@@ -290,9 +296,8 @@ __global__ void __launch_bounds__(OS_THREADS,
                                                : (const void *)(p.keys_in + tile_base);
     const void *vsrc = kGen ? nullptr : (const void *)(p.vals_in + tile_base);
     const void *usrc = !kUV ? nullptr
-                            : kGen ? (const void *)(p.u + tile_base) : (const void *)(p.pu_in + tile_base);
-    const void *wsrc = !kUV ? nullptr
-                            : kGen ? (const void *)(p.v + tile_base) : (const void *)(p.pv_in + tile_base);
+                            : kGen ? (const void *)(p.u + tile_base) : (const void *)(p.uv_in + tile_base);
+    const void *wsrc = kUV && kGen ? (const void *)(p.v + tile_base) : nullptr;
     const bool k_bulk = (((uintptr_t)ksrc) & 15) == 0;
     const bool v_bulk = !kGen && (((uintptr_t)vsrc) & 15) == 0;
     const bool uv_bulk = kUV && ((((uintptr_t)usrc | (uintptr_t)wsrc) & 15) == 0);
@@ -306,8 +311,12 @@ __global__ void __launch_bounds__(OS_THREADS,
             if (v_bulk)
                 tma_load_1d(B1, vsrc, bytes, &s_bar[1]);
             if (uv_bulk) {
-                tma_load_1d(B2, usrc, bytes, &s_bar[1]);
-                tma_load_1d(B3, wsrc, bytes, &s_bar[1]);
+                if (kGen) {
+                    tma_load_1d(B3, usrc, bytes, &s_bar[1]);
+                    tma_load_1d(B4, wsrc, bytes, &s_bar[1]);
+                } else {
+                    tma_load_1d(B3, usrc, 2u * bytes, &s_bar[1]);   // int2 per element
+                }
             }
         }
     }
@@ -320,8 +329,12 @@ __global__ void __launch_bounds__(OS_THREADS,
             B1[i] = p.vals_in[tile_base + i];
     if (kUV) {
         for (int i = (uv_bulk ? n_bulk : 0) + tid; i < tile_count; i += OS_THREADS) {
-            B2[i] = kGen ? (u32)p.u[tile_base + i] : p.pu_in[tile_base + i];
-            B3[i] = kGen ? (u32)p.v[tile_base + i] : p.pv_in[tile_base + i];
+            if (kGen) {
+                B3[i] = (u32)p.u[tile_base + i];
+                B4[i] = (u32)p.v[tile_base + i];
+            } else {
+                ((int2 *)B3)[i] = p.uv_in[tile_base + i];
+            }
         }
     }
     // global start of every owned digit's bucket: scanned once per pass when
@@ -401,7 +414,7 @@ __global__ void __launch_bounds__(OS_THREADS,
     }
     __syncthreads();
 
-    // ---- keys into B4 in digit order ------------------------------------------
+    // ---- keys into KD in digit order ------------------------------------------
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
         const int i = wbase + it * 32 + lane;
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(OS_THREADS,
             const u32 key = key_at(i);
             const u32 d = (key >> shift) & DMASK;
             const u32 pos = s_local_start[d] + s_whist[warp][d] + lpos[it];
-            B4[pos] = key;
+            KD[pos] = key;
             if (!L::kWide)
                 s_dig[pos] = (unsigned char)d;
             lpos[it] = pos;
@@ -467,12 +480,12 @@ __global__ void __launch_bounds__(OS_THREADS,
     mbar_wait_bounded(&s_bar[1], 0, p.status);   // value streams landed
     __syncthreads();
 
-    // ---- write keys (B4); values, stream 0, into B0 in digit order ------------
-    // digit of output position j (B4 keeps the keys in digit order)
-    auto dig_at = [&](int j) -> u32 { return L::kWide ? (B4[j] >> shift) & DMASK : (u32)s_dig[j]; };
+    // ---- write keys (KD); values, stream 0, into B0 in digit order ------------
+    // digit of output position j (KD keeps the keys in digit order)
+    auto dig_at = [&](int j) -> u32 { return L::kWide ? (KD[j] >> shift) & DMASK : (u32)s_dig[j]; };
     if (FLAGS & OS_WRITE_KEYS) {
         for (int j = tid; j < tile_count; j += OS_THREADS)
-            p.keys_out[s_goff[dig_at(j)] + (u32)j] = B4[j];
+            p.keys_out[s_goff[dig_at(j)] + (u32)j] = KD[j];
     }
 #pragma unroll
     for (int it = 0; it < OS_ITEMS; ++it) {
@@ -482,7 +495,7 @@ __global__ void __launch_bounds__(OS_THREADS,
     }
     __syncthreads();
 
-    // ---- write values (B0); u, v into B1, B4 in digit order -------------------
+    // ---- write values (B0); endpoints into B1..B2 in digit order --------------
     for (int j = tid; j < tile_count; j += OS_THREADS)
         p.vals_out[s_goff[dig_at(j)] + (u32)j] = B0[j];
     if (kUV) {
@@ -490,7 +503,15 @@ __global__ void __launch_bounds__(OS_THREADS,
         for (int it = 0; it < OS_ITEMS; ++it) {
             const int i = wbase + it * 32 + lane;
             if (i < tile_count) {
-                u32 xa = B2[i], xb = B3[i];
+                u32 xa, xb;
+                if (kGen) {
+                    xa = B3[i];
+                    xb = B4[i];
+                } else {
+                    const int2 e = ((const int2 *)B3)[i];
+                    xa = (u32)e.x;
+                    xb = (u32)e.y;
+                }
                 if (kGen) {
                     // first pass: validate the caller's endpoints and turn
                     // tree-local ids into forest ids
@@ -521,20 +542,14 @@ __global__ void __launch_bounds__(OS_THREADS,
                     xa = (u32)(a + voff);
                     xb = (u32)(b + voff);
                 }
-                B1[lpos[it]] = xa;
-                B4[lpos[it]] = xb;
+                ((int2 *)B1)[lpos[it]] = make_int2((i32)xa, (i32)xb);
             }
         }
         __syncthreads();
-        for (int j = tid; j < tile_count; j += OS_THREADS) {
-            const u32 pos = s_goff[s_dig[j]] + (u32)j;
-            if (kAB) {
-                p.ab_out[pos] = make_int2((i32)B1[j], (i32)B4[j]);
-            } else {
-                p.pu_out[pos] = B1[j];
-                p.pv_out[pos] = B4[j];
-            }
-        }
+        // the last pass writes the level-0 edge array, the others the next
+        // pass's endpoint stream: both an int2 per edge
+        for (int j = tid; j < tile_count; j += OS_THREADS)
+            p.uv_out[s_goff[s_dig[j]] + (u32)j] = ((const int2 *)B1)[j];
     }
 }
 
