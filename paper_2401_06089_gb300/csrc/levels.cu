@@ -31,6 +31,16 @@
 
 #include "kernels.cuh"
 
+// Resident blocks of 256 threads per SM the tile-ranking level kernels
+// (ptr_init, compact) are compiled for (40 registers): their tiles wait on
+// dependent loads and block barriers, so more resident tiles hide more of
+// it.  At 10^8 edges, random recursive tree: ptr_init 1.71 -> 1.55 ms,
+// compact 3.79 -> 3.38 ms against the unconstrained 48 and 63 registers
+// (4 and 5 blocks resident); 5 and 8 blocks were slower than 6.
+#ifndef PANDORA_LV_MINB
+#define PANDORA_LV_MINB 6
+#endif
+
 namespace pandora {
 
 namespace {
@@ -115,7 +125,7 @@ __device__ __forceinline__ u32 claim_tile(u32 *counter, u32 *s_tile)
 }
 
 template <bool LEVEL0, bool FOREST>
-__global__ void __launch_bounds__(LV_THREADS) ptr_init_kernel(const LevelParams p)
+__global__ void __launch_bounds__(LV_THREADS, PANDORA_LV_MINB) ptr_init_kernel(const LevelParams p)
 {
     if (loop_closed(p))
         return;
@@ -432,7 +442,7 @@ __device__ __forceinline__ i32 sv_of(const LevelParams &p, i32 x, u64 n_next)
 }
 
 template <bool LEVEL0>
-__global__ void __launch_bounds__(LV_THREADS) compact_kernel(const LevelParams p)
+__global__ void __launch_bounds__(LV_THREADS, PANDORA_LV_MINB) compact_kernel(const LevelParams p)
 {
     if (loop_closed(p))
         return;
