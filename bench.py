@@ -274,6 +274,40 @@ def model_bytes(name, prof_entry, m, n_passes_w, level0_calls=0, m1=0):
     return MODEL_BYTES.get(name, 0) * e
 
 
+def dendrogram_height(edge_parent, vertex_parent):
+    """Height of a dendrogram (Section 3.1, skewness): the most edge nodes on
+    a path from the root edge down to a vertex.  Depths of the edges by
+    pointer jumping on edge_parent (torch, on the tensors' device: a
+    measurement of the output, not part of the timed path); a vertex sits one
+    below its parent edge."""
+    import torch
+    ep = edge_parent.to(torch.int64)
+    m = ep.numel()
+    if m == 0:
+        return 0
+    idx = torch.arange(m, device=ep.device)
+    root = ep < 0
+    p = torch.where(root, idx, ep)
+    d = (~root).to(torch.int64)            # edges between i and p[i]
+    for _ in range(64):
+        pp = p[p]
+        if torch.equal(pp, p):
+            break
+        d = d + d[p]
+        p = pp
+    vp = vertex_parent.to(torch.int64)
+    return int((d[vp[vp >= 0]] + 1).max().item())
+
+
+def skewness(edge_parent, vertex_parent):
+    """{height, ideal = log2 n, ratio}: the paper's skewness measure."""
+    import math
+    n = vertex_parent.numel()
+    h = dendrogram_height(edge_parent, vertex_parent)
+    ideal = math.log2(n) if n > 1 else 1.0
+    return {"height": h, "ideal_log2_n": round(ideal, 3), "ratio": round(h / ideal, 2)}
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary of `kernel`, or None
     when the kernel's source changed since the counters were taken."""
@@ -494,6 +528,7 @@ def measure_hdbscan(pd, torch, args, n_points=None, reps=20, mcs=16):
                               "clusters": int(lab.max()) + 1,
                               "noise_fraction": float((lab < 0).mean())},
             "pipeline_ms": emst + ms + flat_ms,
+            "skewness": skewness(ep, vp),
             "structure_ok": st["ok"]}
 
 
@@ -1095,6 +1130,7 @@ def main():
         "api": "pandora_dendrogram_async" if args.async_api else "pandora_dendrogram",
         "graph_ms_per_step": graph_ms if args.async_api else None,
         "levels": stats["level_edges"],
+        "skewness": skewness(ep, vp),
         "clocks": sampler.summary(),
     }
 
@@ -1149,7 +1185,8 @@ def main():
         ms2 = a.elapsed_time(b) / k2
         _, _, st2 = pd.dendrogram(u2, v2, w2, workspace=ws, out=(ep, vp), stats=True)
         line["path_skewed_1e8"] = {"value": t2.m / (ms2 / 1e3), "unit": UNIT, "ms_per_step": ms2,
-                                   "steps": k2, "levels": st2["level_edges"]}
+                                   "steps": k2, "levels": st2["level_edges"],
+                                   "skewness": skewness(ep, vp)}
         del u2, v2, w2
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1) -------------------

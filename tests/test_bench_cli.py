@@ -1,9 +1,11 @@
 """The benchmark's reference arm runs on the CPU: its JSON line carries the
-keys the benchmark contract asks for."""
+keys the benchmark contract asks for; and the benchmark's host-side helpers."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -64,3 +66,26 @@ def test_structure_check_accepts_dendrograms_and_rejects_corruptions():
     one = check(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.float32),
                 np.zeros(0, np.int32), np.full(1, -1, np.int32))
     assert one["ok"]
+
+
+def test_dendrogram_height_and_skewness():
+    """The skewness the bench reports (Section 3.1: height over log2 n) on
+    dendrograms whose height is known: a chain and a balanced tree."""
+    torch = pytest.importorskip("torch")
+    sys.path.insert(0, ROOT)
+    import bench
+    # a chain: e0 -> e1 -> e2 -> e3 (root); vertices 0, 1 under e0, then one
+    # vertex under each further edge: the deepest vertex is 4 edges down
+    ep = torch.tensor([1, 2, 3, -1])
+    vp = torch.tensor([0, 0, 1, 2, 3])
+    assert bench.dendrogram_height(ep, vp) == 4
+    # balanced: root e1 over e0 and e2, two vertices under each
+    ep = torch.tensor([1, -1, 1])
+    vp = torch.tensor([0, 0, 2, 2])
+    assert bench.skewness(ep, vp) == {"height": 2, "ideal_log2_n": 2.0, "ratio": 1.0}
+    # a long chain, deeper than a single pointer-jumping step
+    m = 1000
+    ep = torch.arange(1, m + 1)
+    ep[-1] = -1
+    vp = torch.cat([torch.tensor([0]), torch.arange(m)])
+    assert bench.dendrogram_height(ep, vp) == m
