@@ -524,6 +524,7 @@ def measure_hdbscan(pd, torch, args, n_points=None, reps=20, mcs=16):
                     "reading), computed on the GPU",
             "emst_ms": emst, "emst_points_per_s": n / (emst / 1e3),
             "emst_timing": "wall clock around the blocking call, median of 3",
+            "emst_bound": EMST_BOUND,
             "flat_clusters": {"min_cluster_size": mcs, "ms_per_call": flat_ms,
                               "clusters": int(lab.max()) + 1,
                               "noise_fraction": float((lab < 0).mean())},
@@ -946,6 +947,15 @@ def run_membench(args):
                       "results": res}), flush=True)
 
 
+# What bounds the spanning-tree traversals (k-NN and Boruvka queries, over
+# 90% of the call; ncu summary in profiles/emst_gmm_4e6.md): neither DRAM nor
+# arithmetic, so no roofline fraction applies.
+EMST_BOUND = {"kind": "latency",
+              "detail": "divergent BVH traversals: k-NN kernel at 1e6 points 0.2% of DRAM peak, "
+                        "L1 hit rate 94%, 9.9 of 32 lanes active per instruction",
+              "profile": "profiles/emst_gmm_4e6.md"}
+
+
 def run_emst(args):
     import numpy as np
     import torch
@@ -966,7 +976,8 @@ def run_emst(args):
                       "value": args.emst / (ms / 1e3), "unit": "points/s", "ms": ms,
                       "steps": args.steps, "n_points": args.emst, "min_pts": 16,
                       "data": "synthetic 32-component Gaussian mixture, seed 3",
-                      "timing": "wall clock around the blocking call, median"}), flush=True)
+                      "timing": "wall clock around the blocking call, median",
+                      "bound": EMST_BOUND}), flush=True)
 
 
 def main():
