@@ -136,3 +136,35 @@ def test_planned_host_offsets_checked_before_any_launch(lib):
                                                   null) == 1
     assert bl.pandora_dendrogram_batched_planned(*args, good, 3, 10, fake, fake, null, 0,
                                                   null) == 9
+
+
+def test_sort_pairs_workspace_follows_the_digit_plan(lib):
+    """pandora_sort_pairs_workspace_size is host-only.  Keys of 25 to 27 bits
+    take three passes of 9-bit digits, whose look-back table has 512 entries
+    per 4096-key tile against 256 for the 8-bit plans (up to 24 and from 28
+    bits): the workspace grows by exactly that table.  Bad arguments are
+    rejected before any launch."""
+    bl = _binding.load_library()
+    sz = ctypes.c_size_t(0)
+
+    def ws(n, bits):
+        assert bl.pandora_sort_pairs_workspace_size(n, bits, ctypes.byref(sz)) == 0
+        return sz.value
+
+    n = 4096 * 1000
+    tiles = 1000
+    base = ws(n, 24)
+    assert ws(n, 28) == base == ws(n, 32) == ws(n, 8)
+    for bits in (25, 26, 27):
+        assert ws(n, bits) == base + tiles * (512 - 256) * 8
+    assert ws(2 * n, 24) > base
+    null = ctypes.c_void_p(0)
+    for args in ((-1, 24), (10, 0), (10, 33)):
+        assert bl.pandora_sort_pairs_workspace_size(*args, ctypes.byref(sz)) == 1
+    assert bl.pandora_sort_pairs_workspace_size(10, 24, ctypes.POINTER(ctypes.c_size_t)()) == 1
+    # the sort itself: bad sizes and null arrays are rejected on the host
+    sort = bl.pandora_sort_pairs
+    assert sort(null, null, -1, 24, null, null, null, 0, null) == 1
+    assert sort(null, null, 10, 24, null, null, null, 0, null) == 1
+    assert sort(null, null, 10, 40, null, null, null, 0, null) == 1
+    assert sort(null, null, 0, 24, null, null, null, 0, null) == 0
